@@ -1,0 +1,401 @@
+"""Benchmark: operator applies/s and time-to-1e-8 residual on one GB300.
+
+Workload (default): anisotropic Helmholtz vector VIE, 128^3 grid on [-1,1]^3,
+4 wavelengths across the box, multi-bump complex-symmetric medium, unit plane
+wave along a seeded direction (the Helmholtz 128^3 configuration).
+
+A "step" is one operator apply y = (I + B + K) x at FP32 (the inner apply of
+the mixed-precision solve).  ``value`` = whole-job applies/s (device time,
+CUDA events, max over ranks).  Extra keys report the FP64 apply rate, the
+time-to-1e-8 residual of mixed vs FP64 solves (p50/p99), per-kernel timing
+and the roofline of the dominant kernel, the oracle timed on the host cores
+(``cpu_baseline``) and an end-to-end rate through the C ABI with host buffers
+(``e2e``).
+
+Multi-GPU: the workload does not shard (no collective in the method's data
+path); N ranks run N independent replicas and ``value`` sums their applies.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BUFS = 8  # rotating input/output buffers: 8 x 2 x 50 MB > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--solves", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n, c, esz):
+    """Bytes each pass must move (values per grid point x N x element size).
+
+    P1 reads c N, writes 2c N; P2 reads 2c N, writes 4c N; P3 reads and writes
+    4c N plus the 6 kernel octants ((n+1)^3 each); P4 reads 4c N, writes 2c N;
+    P5 reads 2c N + x (c N) + H (6 N), writes c N.
+    """
+    N = n ** 3
+    O3 = (n + 1) ** 3
+    return [3 * c * N * esz, 6 * c * N * esz, (8 * c * N + 6 * O3) * esz, 6 * c * N * esz, (4 * c * N + 6 * N) * esz]
+
+
+def pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[k]
+
+
+def cpu_baseline_oracle(n, reps, seconds_cap=30.0):
+    """FP64 oracle applies on the host cores (untimed set-up, timed applies)."""
+    import numpy as np
+    import scipy.fft  # noqa: F401
+
+    import vie_inputs as vi
+    from oracle import operators, discrete
+
+    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
+    op = operators.OracleProblem.from_problem(p)
+    x = vi.random_field(n, 3, 0)[0]
+    op.apply(x)  # builds the kernel transforms (set-up, untimed)
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        op.apply(x)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > seconds_cap:
+            break
+    tot = sum(times)
+    return {"value": len(times) / tot, "unit": "applies/s", "cores": discrete.WORKERS, "kind": "oracle",
+            "sample": f"{len(times)} FP64 oracle applies of the {n}^3 Helmholtz workload after untimed set-up "
+                      f"({tot:.1f} s)", "applies": len(times), "seconds": tot}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import vie_inputs as vi
+    from oracle import operators, discrete
+
+    n = args.n
+    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
+    op = operators.OracleProblem.from_problem(p)
+    x = vi.random_field(n, 3, 0)[0]
+    # each step is one FP64 oracle apply (~seconds at 128^3); the run is bounded
+    # to about a minute of timed work, so fewer than --steps may be timed
+    for _ in range(min(args.warmup, 1)):
+        op.apply(x)
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        op.apply(x)
+        done += 1
+        if time.perf_counter() - t0 > 60.0:
+            break
+    dt = time.perf_counter() - t0
+    args.steps = done
+    v = done / dt
+    cores = discrete.WORKERS
+    line = {"impl": "reference", "metric": "operator applies/s", "value": v, "unit": "applies/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": f"helmholtz_multibump_{n}", "n": n, "wavelengths": 4.0,
+                                             "precision": "fp64", "box": [-1.0, 1.0]},
+            "cpu_baseline": {"value": v, "unit": "applies/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle applies at {n}^3 after untimed set-up"},
+            "e2e": {"value": v, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    n = args.n
+    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
+    eps = torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev)
+    t0 = time.perf_counter()
+    P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, eps)
+    t_setup = time.perf_counter() - t0
+    del eps
+    c = P.ncomp
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + rank)
+    xs = [torch.randn((c, n, n, n), dtype=torch.complex64, device=dev, generator=g) for _ in range(N_BUFS)]
+    ys = [torch.empty_like(xs[0]) for _ in range(N_BUFS)]
+
+    def step(i, prec=vie.VIE_FP32):
+        P.apply(xs[i % N_BUFS], ys[i % N_BUFS], prec)
+
+    # ---------------- FP32 apply (the metric's step)
+    for i in range(max(3, args.warmup)):
+        step(i)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step(i)
+        ends[i].record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    applies_per_s = world * args.steps / (total_ms / 1000.0)
+
+    # ---------------- per-kernel timing of the same workload (event-bracketed passes)
+    kreps = min(args.steps, 100)
+    vie.vie_profile_begin(P.handle, kreps)
+    for i in range(kreps):
+        step(i)
+    pass_ms, cnt = vie.vie_profile_end(P.handle)
+    pass_avg = [m / max(cnt, 1) for m in pass_ms]
+
+    # ---------------- FP64 apply rate
+    xs64 = [x.to(torch.complex128) for x in xs[:2]]
+    ys64 = [torch.empty_like(xs64[0]) for _ in range(2)]
+    for i in range(3):
+        P.apply(xs64[i % 2], ys64[i % 2], vie.VIE_FP64)
+    torch.cuda.synchronize()
+    k64 = max(5, min(40, args.steps // 5))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(k64):
+        P.apply(xs64[i % 2], ys64[i % 2], vie.VIE_FP64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / k64
+    del xs64, ys64
+
+    # ---------------- end to end through the C ABI with host buffers
+    xh = [torch.empty((c, n, n, n), dtype=torch.complex64, pin_memory=True) for _ in range(2)]
+    yh = [torch.empty_like(xh[0]) for _ in range(2)]
+    for i in range(2):
+        xh[i].copy_(xs[i].cpu())
+    xd, yd = xs[0], ys[0]
+    ke = max(5, min(50, args.steps // 4))
+    for i in range(2):
+        xd.copy_(xh[i], non_blocking=True)
+        P.apply(xd, yd, vie.VIE_FP32)
+        yh[i].copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for i in range(ke):
+        xd.copy_(xh[i % 2], non_blocking=True)
+        P.apply(xd, yd, vie.VIE_FP32)
+        yh[i % 2].copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te
+    e2e = {"value": world * ke / te, "unit": "applies/s", "h2d_bytes_per_step": xh[0].numel() * 8,
+           "d2h_bytes_per_step": yh[0].numel() * 8}
+    del xh, yh
+
+    # ---------------- time to 1e-8 residual, mixed vs FP64
+    solve = None
+    if not args.no_solve:
+        b = torch.empty((c, n, n, n), dtype=torch.complex128, device=dev)
+        P.rhs(p.directions[0], None, 1, b)
+        J = torch.zeros_like(b)
+        res = {}
+        for mode, name, reps in ((vie.VIE_SOLVE_MIXED, "mixed", args.solves),
+                                 (vie.VIE_SOLVE_FP64, "fp64", max(3, args.solves // 3))):
+            ts, infos = [], []
+            for r in range(reps + 1):
+                J.zero_()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                st, info = P.solve(b, J, tol=1e-8, restart=50, max_outer=40, max_inner=3000, inner_tol=1e-5,
+                                   mode=mode)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t1
+                if r > 0:  # first solve allocates the Krylov basis
+                    ts.append(dt)
+                    infos.append(info.as_dict())
+            res[name] = {"p50_s": pct(ts, 50), "p99_s": pct(ts, 99), "solves": len(ts),
+                         "rel_residual": infos[-1]["rel_residual"], "applies_fp32": infos[-1]["applies_fp32"],
+                         "applies_fp64": infos[-1]["applies_fp64"], "gmres_iters": infos[-1]["inner_iters"]}
+        res["speedup_p50"] = res["fp64"]["p50_s"] / res["mixed"]["p50_s"]
+        solve = res
+
+    # ---------------- roofline of the dominant kernel
+    peak, peak_src = load_peaks()
+    names = ["P1_fwd_x", "P2_fwd_y", "P3_z_kernel_z", "P4_inv_y", "P5_inv_x_epilogue"]
+    abytes = algorithmic_bytes(n, c, 8)
+    dom = max(range(5), key=lambda k: pass_avg[k])
+    achieved = abytes[dom] / (pass_avg[dom] / 1000.0) / 1e9
+    kernels = {names[k]: {"avg_ms": pass_avg[k], "alg_bytes": abytes[k],
+                          "gbs": abytes[k] / (pass_avg[k] / 1000.0) / 1e9 if pass_avg[k] > 0 else None}
+               for k in range(5)}
+    apply_bytes = sum(abytes)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(n, reps=5)
+
+    if rank == 0:
+        line = {
+            "metric": "operator applies/s (FP32 apply of the mixed solve) & time-to-1e-8 residual (mixed vs FP64)",
+            "value": applies_per_s, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "p50_ms": pct(per, 50), "p99_ms": pct(per, 99),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic",
+            "config": {"workload": f"helmholtz_multibump_{n}", "n": n, "wavelengths": 4.0, "box": [-1.0, 1.0],
+                       "components": c, "precision": "fp32 apply (FP64 set-up)",
+                       "l2": f"inputs/outputs rotate over {N_BUFS} buffer pairs ({N_BUFS * 2 * xs[0].numel() * 8 / 1e6:.0f} MB > L2)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "fp64_apply": {"ms": fp64_ms, "applies_per_s": 1000.0 / fp64_ms},
+            "apply_alg_bytes": apply_bytes, "apply_alg_gbs": apply_bytes / (total_ms / args.steps / 1000.0) / 1e9,
+            "kernels": kernels,
+            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": None},
+            "solve": solve, "setup_s": t_setup, "wall_s_timed": t_wall,
+            "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

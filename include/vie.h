@@ -1,0 +1,167 @@
+/* vie.h -- C ABI of the GB300 (sm_103a) FFT-accelerated volume integral
+ * equation solver for anisotropic, inhomogeneous media.
+ *
+ * Method: Imbert-Gerard, Vico, Greengard, Ferrando, "Integral equation methods
+ * for electrostatics, acoustics and electromagnetics in smoothly varying,
+ * anisotropic media" (arXiv:1805.04791).  The library solves the second-kind
+ * equations (I + B + K) J = b of
+ *   - Eq. (eq:intLap)  Laplace:   J - 2 H_eps T_0 J = 2 H_eps grad phi_in,
+ *   - Eq. (eq:intH)    Helmholtz: J - 2 H_{eps^-1} T_w J = 2 H_{eps^-1} grad phi_in
+ *                      (sign as produced by the derivation of Sec. 3; the
+ *                      printed equation carries "+"),
+ *   - Eq. (eq:intM)    Maxwell:   the coupled [J; M] system, or Eq.
+ *                      (contraction_Maxwell_reduced) when mu = I,
+ * with H_eps = (eps + I)^-1 (eps - I) (Eq. (rhodef)) and T J = J/2 + grad div V J
+ * (Eqs. (Todef), (Vw)).  The volume potentials are applied with the
+ * truncated-kernel FFT method of Sec. 5 (truncate the Green's function at
+ * L = sqrt(3) D, transform it, cut off at the grid Nyquist frequency) on a
+ * uniform cell-centred n^3 grid, as zero-padded convolutions on a (2n)^3 grid.
+ *
+ * Conventions common to every call
+ * --------------------------------
+ * - Complex numbers are interleaved (re, im): FP64 = 16 bytes, FP32 = 8 bytes.
+ * - Grid arrays are [z][y][x], x fastest; node i sits at lo + (i + 1/2) h.
+ * - A vector field with c components is [c][n][n][n]; a batch of nrhs fields
+ *   is [nrhs][c][n][n][n] (batch outermost).  c = 3 for Laplace, Helmholtz
+ *   and Maxwell with mu = I; c = 6 ([J; M]) for Maxwell with mu.
+ * - "device" pointers are CUDA device memory of the current device; the
+ *   caller owns every pointer it passes in (the library never frees them).
+ *   The library owns everything it allocates, from create until destroy.
+ * - stream is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *   work on it and return without synchronising unless stated otherwise.
+ * - No exception crosses the ABI; every call returns a vie_status and, on
+ *   failure, vie_last_error() returns a message (thread-local).
+ * - A problem handle is not thread-safe; distinct handles may be used from
+ *   different threads on different streams.
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VIE_OK = 0,
+  VIE_EINVAL = 1,   /* bad argument (size, pointer, symmetry, precision) */
+  VIE_ENOMEM = 2,   /* device allocation failed */
+  VIE_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  VIE_ENOCONV = 4,  /* solver hit its iteration limit before the tolerance */
+  VIE_ENAN = 5,     /* non-finite values met in a solve */
+  VIE_ETIMEOUT = 6, /* a bounded device wait expired */
+  VIE_EBUSY = 7     /* resource in use */
+} vie_status;
+
+typedef enum { VIE_LAPLACE = 0, VIE_HELMHOLTZ = 1, VIE_MAXWELL = 2 } vie_kind;
+
+/* Arithmetic of an operator apply: FP64 complex, or FP32 complex (inner
+ * iterations of the mixed-precision solve). */
+typedef enum { VIE_FP64 = 0, VIE_FP32 = 1 } vie_precision;
+
+/* Solver modes for vie_solve: plain FP64 GMRES(m), or FP32-inner GMRES(m)
+ * inside an FP64 iterative-refinement loop. */
+typedef enum { VIE_SOLVE_FP64 = 0, VIE_SOLVE_MIXED = 1 } vie_solve_mode;
+
+typedef struct vie_problem vie_problem;
+
+typedef struct {
+  double tol;        /* stop when ||b - A J||_2 / ||b||_2 <= tol (FP64 residual) */
+  int restart;       /* GMRES restart length m (1..200) */
+  int max_outer;     /* mixed: maximum refinement steps; FP64: maximum restarts */
+  int max_inner;     /* maximum GMRES iterations per refinement step (mixed) or in total (FP64) */
+  double inner_tol;  /* mixed: relative tolerance of each inner FP32 solve */
+  int mode;          /* vie_solve_mode */
+  int nrhs;          /* number of right-hand sides, solved independently (>= 1) */
+} vie_solve_opts;
+
+typedef struct {
+  int outer_iters;        /* refinement steps (mixed) or restarts (FP64) */
+  int inner_iters;        /* GMRES iterations (= FP32 or FP64 applies inside Arnoldi) */
+  int applies_fp32;
+  int applies_fp64;
+  double rel_residual;    /* max over right-hand sides of the final FP64 relative residual */
+  double t_solve;         /* wall seconds spent in vie_solve */
+} vie_solve_info;
+
+/* Create a problem: grid, medium and frequency (Sec. 2 / Eq. (Laplace_Scalar),
+ * Sec. 3 / Eq. (Helmholtz0), Sec. 4 / Eq. (Maxwell)).
+ *   kind   vie_kind.
+ *   n      points per axis, n = 2^a 3^b with 4 <= n <= 256.
+ *   lo, hi box [lo, hi]^3 (hi > lo).
+ *   omega  angular frequency (ignored for Laplace; >= 0).
+ *   eps    device, FP64 complex [9][n][n][n], the 3x3 tensor row-major per node;
+ *          must be symmetric (|eps_ab - eps_ba| <= 1e-12 (1 + |eps|)), eps + I
+ *          invertible.  Laplace uses the real part.
+ *   mu     device, same layout, or NULL for mu = I (Maxwell only; other kinds ignore it).
+ * Computes H_eps (and H_mu) per node (Eq. (rhodef)) and the transforms of the
+ * truncated kernels (Sec. 5) in FP64 on the device; keeps FP64 and FP32 copies.
+ * Synchronises the stream.  *out receives the handle. */
+vie_status vie_problem_create(int kind, int n, double lo, double hi, double omega, const void* eps, const void* mu,
+                              void* stream, vie_problem** out);
+
+/* Number of unknown components c (3 or 6) of a problem. */
+int vie_problem_ncomp(const vie_problem* P);
+
+/* y = (I + B + K) x, the left-hand side of Eq. (eq:intLap), (eq:intH) or (eq:intM).
+ *   x, y   device, [nrhs][c][n][n][n], FP64 complex (precision VIE_FP64) or FP32
+ *          complex (VIE_FP32); x and y must not overlap.
+ *   nrhs   >= 1.  Asynchronous on stream. */
+vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
+
+/* Right-hand sides for plane-wave (or uniform-field) incidence, FP64 complex,
+ * [nrhs][c][n][n][n] into device buffer rhs_out.
+ *   d  host, [nrhs][3]: Laplace: the applied field E0 (grad phi_in = -E0);
+ *      Helmholtz / Maxwell: unit propagation direction, phi_in = exp(i w d.x).
+ *   p  host, [nrhs][3]: Maxwell polarisation (E_in = p exp(i w d.x),
+ *      H_in = d x p exp(i w d.x)); ignored otherwise (may be NULL).
+ * Laplace: 2 H_eps grad phi_in (Eq. (eq:intLap)); Helmholtz: 2 H_{eps^-1} grad phi_in
+ * (Eq. (eq:intH)); Maxwell: [2 H_eps E_in; 2 H_mu H_in] (Eq. (eq:intM)). */
+vie_status vie_rhs_plane_wave(vie_problem* P, const double* d, const double* p, int nrhs, void* rhs_out,
+                              void* stream);
+
+/* Solve (I + B + K) J = rhs by restarted GMRES (Sec. 1 and Sec. 6 name GMRES for
+ * these second-kind equations).
+ *   rhs  device, FP64 complex [nrhs][c][n][n][n].
+ *   J    device, same layout: initial guess on entry (zeros for none), solution on exit.
+ *   opt  solver options (nrhs from opt->nrhs); info may be NULL.
+ * Synchronises the stream.  Returns VIE_ENOCONV (J holds the last iterate) if a
+ * right-hand side misses the tolerance, VIE_ENAN on non-finite residuals. */
+vie_status vie_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_opts* opt, vie_solve_info* info,
+                     void* stream);
+
+/* Scattered field from the solved density, FP64 complex on the grid.
+ *   Laplace / Helmholtz: phi_sc = div V J, 1 component (Sec. 2 existence proof;
+ *     summary after Eq. (eq:intH)); field_out [nrhs][1][n][n][n].
+ *   Maxwell: [E_sc; H_sc] by Eq. (represent_Maxwell) (or Eq.
+ *     (represent_Maxwell_reduced) when mu = I); field_out [nrhs][6][n][n][n].
+ * Asynchronous on stream. */
+vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, int nrhs, void* stream);
+
+/* Device bytes a problem of this shape holds (medium, kernels, apply workspace
+ * for nrhs right-hand sides, FP32 Krylov basis of length restart); used for
+ * admission by memory budget.  has_mu: 1 for Maxwell with mu. */
+size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu);
+
+/* Release every allocation of the handle (synchronises the device). */
+vie_status vie_problem_destroy(vie_problem* P);
+
+/* Per-kernel timing of vie_apply / vie_eval_scattered, for measurement tools.
+ * vie_profile_begin(P, cap) makes the following applies on P record a CUDA
+ * event before and after each of their kernel launches (on the launch stream;
+ * no synchronisation), for at most cap applies.  vie_profile_end synchronises
+ * the device, writes into ms[k] (k < nslots, host) the total milliseconds spent
+ * in kernel slot k (0..4: the five passes of the pipeline, see apply.cu),
+ * writes the number of recorded applies to *count, and stops recording. */
+vie_status vie_profile_begin(vie_problem* P, int cap);
+vie_status vie_profile_end(vie_problem* P, double* ms, int nslots, int* count);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* vie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIE_H */

@@ -1,0 +1,374 @@
+// The operator apply (I + B + K) x of Eqs. (eq:intLap), (eq:intH), (eq:intM),
+// and the scattered-field evaluation, as a pruned zero-padded 3D convolution
+// (Sec. 5: the truncated kernel transform applied with the FFT).
+//
+// Five passes over HBM, all shared-memory tiled with mixed-radix Stockham
+// FFTs (vie_fft.cuh):
+//   P1  x-lines: zero-pad n -> 2n, forward FFT          x [c][n][n][n]    -> A [c][n][n][2n]
+//   P2  y-lines: zero-pad, forward FFT                   A                 -> B [c][n][2n][2n]
+//   P3  z-pencils of all components: zero-pad, forward FFT, per-k kernel
+//       mixing (3x3 symmetric, 6x6 Maxwell, divergence or E/H), inverse
+//       FFT, keep z < n                                  B                 -> B (in place)
+//   P4  y-lines: inverse FFT, keep y < n                 B                 -> A
+//   P5  x-lines of all components: inverse FFT, keep x < n, epilogue
+//       y = x + H u (u the convolution; H per node, 3x3 symmetric)  A      -> y
+// The padded z-planes z >= n are never stored (their input is zero and their
+// output is discarded).  The kernel arrays are octants of the (2n)^3 DFT with
+// the identity part of T, the sign and factor 2 of B, and the 1/(2n)^3 of the
+// inverse DFT folded in.
+#include <algorithm>
+
+#include "vie_internal.h"
+
+namespace vie {
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static const double2* K(const KernelSet& k) { return k.oct64; }
+  static const double2* H(const double2* h64, const float2*) { return h64; }
+  static const double2* tw(const vie_problem* P) { return P->tw64; }
+};
+template <> struct Prec<float> {
+  static const float2* K(const KernelSet& k) { return k.oct32; }
+  static const float2* H(const double2*, const float2* h32) { return h32; }
+  static const float2* tw(const vie_problem* P) { return P->tw32; }
+};
+
+template <typename V>
+__device__ __forceinline__ void load_tw(V* tw, const V* __restrict__ twg, int M) {
+  for (int j = flat_tid(); j < M; j += flat_nthreads()) tw[j] = twg[j];
+}
+
+// ---------------------------------------------------------------- P1
+template <typename T>
+__global__ void k_p1(const typename CT<T>::V* __restrict__ x, typename CT<T>::V* __restrict__ A, int n, FftPlan pl,
+                     const typename CT<T>::V* __restrict__ twg, int nl, int C) {
+  typedef typename CT<T>::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int M = pl.M, LS = M + 1;
+  V* tw = (V*)smraw;
+  V* b0 = tw + M;
+  V* b1 = b0 + nl * LS;
+  load_tw(tw, twg, M);
+  const long long N = (long long)n * n * n;
+  const int c = blockIdx.y, b = blockIdx.z, nc = gridDim.y;
+  const V* src = x + ((long long)b * nc + c) * N;
+  V* dst = A + ((long long)b * C + c) * ((long long)n * n * M);
+  const int r0 = blockIdx.x * nl;
+  const int rows = n * n;
+  for (int l = threadIdx.y; l < nl; l += blockDim.y) {
+    const int r = r0 + l;
+    for (int j = threadIdx.x; j < M; j += blockDim.x)
+      b0[l * LS + j] = (j < n && r < rows) ? src[(long long)r * n + j] : CT<T>::make(0, 0);
+  }
+  __syncthreads();
+  V* res = tile_fft<-1, T>(b0, b1, pl, tw, nl, LS);
+  for (int l = threadIdx.y; l < nl; l += blockDim.y) {
+    const int r = r0 + l;
+    if (r >= rows) continue;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) dst[(long long)r * M + j] = res[l * LS + j];
+  }
+}
+
+// ---------------------------------------------------------------- P2 / P4
+// Lines along y.  FWD: in = A [bc][z][y<n][kx], out = B [bc][z][ky][kx].
+//                 INV: in = B, out = A (keep y < n).
+template <typename T, int S>
+__global__ void k_py(const typename CT<T>::V* __restrict__ in, typename CT<T>::V* __restrict__ out, int n,
+                     FftPlan pl, const typename CT<T>::V* __restrict__ twg, int nl, int C, int ncomp) {
+  typedef typename CT<T>::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int M = pl.M, LS = M + 1;
+  V* tw = (V*)smraw;
+  V* b0 = tw + M;
+  V* b1 = b0 + nl * LS;
+  load_tw(tw, twg, M);
+  const int kx0 = blockIdx.x * nl, z = blockIdx.y;
+  const int bc = blockIdx.z;  // rhs * ncomp + comp
+  const int b = bc / ncomp, c = bc - b * ncomp;
+  const long long plane = ((long long)b * C + c) * n + z;  // index of the (bc, z) slab
+  const int nin = (S < 0) ? n : M;                          // input rows
+  const int nout = (S < 0) ? M : n;                         // output rows
+  const V* src = in + plane * (long long)nin * M;
+  V* dst = out + plane * (long long)nout * M;
+  const int tid = flat_tid(), nt = flat_nthreads();
+  for (int idx = tid; idx < nl * M; idx += nt) {
+    const int j = idx / nl, l = idx - j * nl;
+    b0[l * LS + j] = (j < nin) ? src[(long long)j * M + kx0 + l] : CT<T>::make(0, 0);
+  }
+  __syncthreads();
+  V* res = tile_fft<S, T>(b0, b1, pl, tw, nl, LS);
+  for (int idx = tid; idx < nl * nout; idx += nt) {
+    const int j = idx / nl, l = idx - j * nl;
+    dst[(long long)j * M + kx0 + l] = res[l * LS + j];
+  }
+}
+
+// ---------------------------------------------------------------- P3
+template <typename V>
+__device__ __forceinline__ V kval(const V* __restrict__ K, int a, long long O3, int O, int par, int kz, int ky,
+                                  int kx, int n) {
+  const int M = 2 * n;
+  int sgn = 1;
+  int oz = kz, oy = ky, ox = kx;
+  if (kz > n) { oz = M - kz; if (par & 4) sgn = -sgn; }
+  if (ky > n) { oy = M - ky; if (par & 2) sgn = -sgn; }
+  if (kx > n) { ox = M - kx; if (par & 1) sgn = -sgn; }
+  V v = K[a * O3 + ((long long)oz * O + oy) * O + ox];
+  if (sgn < 0) { v.x = -v.x; v.y = -v.y; }
+  return v;
+}
+
+template <typename T>
+__global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const typename CT<T>::V* __restrict__ twg,
+                     int nl, int C, const typename CT<T>::V* __restrict__ K, int mode) {
+  typedef typename CT<T>::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int M = pl.M, LS = M + 1;
+  const int cin = (mode == KM_MAXWELL6) ? 6 : 3;
+  const int cout = (mode == KM_SYM3) ? 3 : (mode == KM_DIV ? 1 : 6);
+  const int cmax = cin > cout ? cin : cout;
+  V* tw = (V*)smraw;
+  V* b0 = tw + M;
+  V* b1 = b0 + cmax * nl * LS;
+  load_tw(tw, twg, M);
+  const int kx0 = blockIdx.x * nl, ky = blockIdx.y, b = blockIdx.z;
+  const long long zs = (long long)M * M;           // z stride within a component
+  const long long cs = (long long)n * zs;          // component stride
+  V* base = B + (long long)b * C * cs + (long long)ky * M + kx0;
+  const int tid = flat_tid(), nt = flat_nthreads();
+  // load: line (c, l) holds z in [0, M)
+  for (int idx = tid; idx < cin * nl * M; idx += nt) {
+    const int l = idx % nl;
+    const int t = idx / nl;
+    const int z = t % M, c = t / M;
+    b0[(c * nl + l) * LS + z] = (z < n) ? base[c * cs + z * zs + l] : CT<T>::make(0, 0);
+  }
+  __syncthreads();
+  V* fw = tile_fft<-1, T>(b0, b1, pl, tw, cin * nl, LS);
+  V* ob = (fw == b0) ? b1 : b0;
+  // per-k mixing
+  const int O = n + 1;
+  const long long O3 = (long long)O * O * O;
+  for (int idx = tid; idx < nl * M; idx += nt) {
+    const int l = idx % nl, kz = idx / nl;
+    const int kx = kx0 + l;
+    V u[6];
+    for (int c = 0; c < cin; ++c) u[c] = fw[(c * nl + l) * LS + kz];
+    V o[6];
+    if (mode == KM_DIV) {
+      V acc = CT<T>::make(0, 0);
+      for (int a = 0; a < 3; ++a) acc = acc + cmul(kval(K, a, O3, O, sym_parity(6 + a), kz, ky, kx, n), u[a]);
+      o[0] = acc;
+    } else {
+      V q[6];
+      for (int a = 0; a < 6; ++a) q[a] = kval(K, a, O3, O, sym_parity(a), kz, ky, kx, n);
+      // symmetric 3x3: [xx xy xz; xy yy yz; xz yz zz]
+      const V qxx = q[0], qyy = q[1], qzz = q[2], qxy = q[3], qxz = q[4], qyz = q[5];
+      o[0] = cmul(qxx, u[0]) + cmul(qxy, u[1]) + cmul(qxz, u[2]);
+      o[1] = cmul(qxy, u[0]) + cmul(qyy, u[1]) + cmul(qyz, u[2]);
+      o[2] = cmul(qxz, u[0]) + cmul(qyz, u[1]) + cmul(qzz, u[2]);
+      if (mode == KM_MAXWELL6 || mode == KM_EMRED) {
+        V p[3];
+        for (int a = 0; a < 3; ++a) p[a] = kval(K, 6 + a, O3, O, sym_parity(6 + a), kz, ky, kx, n);
+        // P x J
+        const V pxj0 = cmul(p[1], u[2]) - cmul(p[2], u[1]);
+        const V pxj1 = cmul(p[2], u[0]) - cmul(p[0], u[2]);
+        const V pxj2 = cmul(p[0], u[1]) - cmul(p[1], u[0]);
+        if (mode == KM_EMRED) {
+          o[3] = CT<T>::make(-pxj0.x, -pxj0.y);
+          o[4] = CT<T>::make(-pxj1.x, -pxj1.y);
+          o[5] = CT<T>::make(-pxj2.x, -pxj2.y);
+        } else {
+          // u[3..5] = M: Q M - P x J ; and add P x M to the J rows
+          o[3] = cmul(qxx, u[3]) + cmul(qxy, u[4]) + cmul(qxz, u[5]) - pxj0;
+          o[4] = cmul(qxy, u[3]) + cmul(qyy, u[4]) + cmul(qyz, u[5]) - pxj1;
+          o[5] = cmul(qxz, u[3]) + cmul(qyz, u[4]) + cmul(qzz, u[5]) - pxj2;
+          o[0] = o[0] + (cmul(p[1], u[5]) - cmul(p[2], u[4]));
+          o[1] = o[1] + (cmul(p[2], u[3]) - cmul(p[0], u[5]));
+          o[2] = o[2] + (cmul(p[0], u[4]) - cmul(p[1], u[3]));
+        }
+      }
+    }
+    for (int c = 0; c < cout; ++c) ob[(c * nl + l) * LS + kz] = o[c];
+  }
+  __syncthreads();
+  V* iv = tile_fft<+1, T>(ob, fw, pl, tw, cout * nl, LS);
+  for (int idx = tid; idx < cout * nl * n; idx += nt) {
+    const int l = idx % nl;
+    const int t = idx / nl;
+    const int z = t % n, c = t / n;
+    base[c * cs + z * zs + l] = iv[(c * nl + l) * LS + z];
+  }
+}
+
+// ---------------------------------------------------------------- P5
+template <typename T>
+__global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename CT<T>::V* __restrict__ xin,
+                     typename CT<T>::V* __restrict__ y, int n, FftPlan pl, const typename CT<T>::V* __restrict__ twg,
+                     int nr, int C, int cout, const typename CT<T>::V* __restrict__ He,
+                     const typename CT<T>::V* __restrict__ Hm, int with_identity) {
+  typedef typename CT<T>::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int M = pl.M, LS = M + 1;
+  V* tw = (V*)smraw;
+  V* b0 = tw + M;
+  V* b1 = b0 + cout * nr * LS;
+  load_tw(tw, twg, M);
+  const int r0 = blockIdx.x * nr, b = blockIdx.y;
+  const int rows = n * n;
+  const long long N = (long long)n * n * n;
+  const long long cs = (long long)rows * M;
+  const V* src = A + (long long)b * C * cs;
+  for (int line = threadIdx.y; line < cout * nr; line += blockDim.y) {
+    const int c = line / nr, r = r0 + line - (line / nr) * nr;
+    for (int j = threadIdx.x; j < M; j += blockDim.x)
+      b0[line * LS + j] = (r < rows) ? src[c * cs + (long long)r * M + j] : CT<T>::make(0, 0);
+  }
+  __syncthreads();
+  V* res = tile_fft<+1, T>(b0, b1, pl, tw, cout * nr, LS);
+  const int tid = flat_tid(), nt = flat_nthreads();
+  for (int idx = tid; idx < nr * n; idx += nt) {
+    const int r = idx / n, xx = idx - r * n;
+    const int row = r0 + r;
+    if (row >= rows) continue;
+    const long long pt = (long long)row * n + xx;
+    V u[6];
+    for (int c = 0; c < cout; ++c) u[c] = res[(c * nr + r) * LS + xx];
+    if (with_identity) {
+      for (int blk = 0; blk < cout / 3; ++blk) {
+        const V* H = blk == 0 ? He : Hm;
+        const V hxx = H[0 * N + pt], hyy = H[1 * N + pt], hzz = H[2 * N + pt];
+        const V hxy = H[3 * N + pt], hxz = H[4 * N + pt], hyz = H[5 * N + pt];
+        const V* xi = xin + ((long long)b * cout + 3 * blk) * N + pt;
+        V* yo = y + ((long long)b * cout + 3 * blk) * N + pt;
+        const V a0 = u[3 * blk], a1 = u[3 * blk + 1], a2 = u[3 * blk + 2];
+        yo[0] = xi[0] + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2);
+        yo[N] = xi[N] + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2);
+        yo[2 * N] = xi[2 * N] + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2);
+      }
+    } else {
+      for (int c = 0; c < cout; ++c) y[((long long)b * cout + c) * N + pt] = u[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host
+static int pow2_divisor(int M, int target) {
+  int nl = target;
+  while (nl > 1 && M % nl != 0) nl >>= 1;
+  return nl;
+}
+
+static dim3 line_block(int M) {
+  int tx = 1;
+  while (tx * 16 < M && tx < 32) tx <<= 1;
+  return dim3(tx, 256 / tx);
+}
+
+size_t apply_workspace_bytes(int n, int c, int nrhs, int prec) {
+  const size_t esz = prec == VIE_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t M = 2 * (size_t)n;
+  return esz * (size_t)nrhs * c * ((size_t)n * n * M + (size_t)n * M * M);
+}
+
+template <typename T>
+static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
+                              bool with_identity, cudaStream_t st) {
+  typedef typename CT<T>::V V;
+  const int n = P->n, M = 2 * n;
+  const int cin = cin_of(K.mode), cout = cout_of(K.mode);
+  const int C = std::max(cin, cout);
+  const size_t need = apply_workspace_bytes(n, C, nrhs, sizeof(T) == 8 ? VIE_FP64 : VIE_FP32);
+  if (P->ws.bytes < need) {
+    if (P->ws.buf) {
+      VIE_CK(cudaStreamSynchronize(st));
+      cudaFree(P->ws.buf);
+      P->ws.buf = nullptr;
+      P->ws.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&P->ws.buf, need);
+    if (e != cudaSuccess) {
+      set_error("out of device memory for the apply workspace");
+      return VIE_ENOMEM;
+    }
+    P->ws.bytes = need;
+  }
+  V* A = (V*)P->ws.buf;
+  V* B = A + (size_t)nrhs * C * n * n * M;
+  const V* tw = Prec<T>::tw(P);
+  const V* Kp = Prec<T>::K(K);
+  const FftPlan& pl = P->plan2n;
+  const dim3 blk = line_block(M);
+  const size_t vs = sizeof(V);
+  Profiler& pf = P->prof;
+  const bool rec = pf.on && pf.count < pf.cap;
+  cudaEvent_t* ev = rec ? &pf.ev[(size_t)pf.count * (kProfSlots + 1)] : nullptr;
+  if (rec) {
+    VIE_CK(cudaEventRecord(ev[0], st));
+    ++pf.count;
+  }
+
+  // P1
+  {
+    const int nl = (int)blk.y;
+    const size_t smem = vs * (M + 2 * nl * (M + 1));
+    VIE_CK(cudaFuncSetAttribute(k_p1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((n * n + nl - 1) / nl, cin, nrhs);
+    k_p1<T><<<grid, blk, smem, st>>>((const V*)in, A, n, pl, tw, nl, C);
+    VIE_CK(cudaGetLastError());
+    if (rec) VIE_CK(cudaEventRecord(ev[1], st));
+  }
+  const int nly = pow2_divisor(M, sizeof(T) == 8 ? 8 : 16);
+  const size_t smem_y = vs * (M + 2 * nly * (M + 1));
+  // P2
+  {
+    VIE_CK(cudaFuncSetAttribute(k_py<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
+    dim3 grid(M / nly, n, nrhs * cin);
+    k_py<T, -1><<<grid, blk, smem_y, st>>>(A, B, n, pl, tw, nly, C, cin);
+    VIE_CK(cudaGetLastError());
+    if (rec) VIE_CK(cudaEventRecord(ev[2], st));
+  }
+  // P3
+  {
+    int nl = pow2_divisor(M, 8);
+    while (nl > 1 && vs * (M + 2 * C * nl * (M + 1)) > 200 * 1024) nl >>= 1;
+    const size_t smem = vs * (M + 2 * C * nl * (M + 1));
+    VIE_CK(cudaFuncSetAttribute(k_p3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(M / nl, M, nrhs);
+    k_p3<T><<<grid, blk, smem, st>>>(B, n, pl, tw, nl, C, Kp, K.mode);
+    VIE_CK(cudaGetLastError());
+    if (rec) VIE_CK(cudaEventRecord(ev[3], st));
+  }
+  // P4
+  {
+    VIE_CK(cudaFuncSetAttribute(k_py<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
+    dim3 grid(M / nly, n, nrhs * cout);
+    k_py<T, +1><<<grid, blk, smem_y, st>>>(B, A, n, pl, tw, nly, C, cout);
+    VIE_CK(cudaGetLastError());
+    if (rec) VIE_CK(cudaEventRecord(ev[4], st));
+  }
+  // P5
+  {
+    int nr = 4;
+    while (nr > 1 && vs * (M + 2 * cout * nr * (M + 1)) > 200 * 1024) nr >>= 1;
+    const size_t smem = vs * (M + 2 * cout * nr * (M + 1));
+    VIE_CK(cudaFuncSetAttribute(k_p5<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((n * n + nr - 1) / nr, nrhs);
+    const V* He = Prec<T>::H(P->He64, P->He32);
+    const V* Hm = P->has_mu ? Prec<T>::H(P->Hm64, P->Hm32) : nullptr;
+    k_p5<T><<<grid, blk, smem, st>>>(A, (const V*)in, (V*)out, n, pl, tw, nr, C, cout, He, Hm,
+                                     with_identity ? 1 : 0);
+    VIE_CK(cudaGetLastError());
+    if (rec) VIE_CK(cudaEventRecord(ev[5], st));
+  }
+  return VIE_OK;
+}
+
+vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
+                     bool with_identity, cudaStream_t st) {
+  if (prec == VIE_FP64) return run_apply_t<double>(P, K, in, out, nrhs, with_identity, st);
+  return run_apply_t<float>(P, K, in, out, nrhs, with_identity, st);
+}
+
+}  // namespace vie

@@ -1,0 +1,223 @@
+// extern "C" entry points of include/vie.h: argument checks, handle life
+// cycle and dispatch to the set-up, apply and solver translation units.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "vie_internal.h"
+
+namespace vie {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+vie_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_ECUDA;
+}
+
+static bool smooth_size(int n) {
+  if (n < 4 || n > 256) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+static void free_set(KernelSet& k) {
+  if (k.oct64) cudaFree(k.oct64);
+  if (k.oct32) cudaFree(k.oct32);
+  k.oct64 = nullptr;
+  k.oct32 = nullptr;
+}
+
+static void free_problem(vie_problem* P) {
+  if (!P) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {P->tw64, P->tw32, P->He64, P->He32, P->Hm64, P->Hm32, P->sym_oct, P->ws.buf, P->ks.buf, P->dflag};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  free_set(P->kapply);
+  free_set(P->keval);
+  for (cudaEvent_t e : P->prof.ev) cudaEventDestroy(e);
+  delete P;
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+extern "C" {
+
+const char* vie_last_error(void) { return g_last_error.c_str(); }
+
+vie_status vie_problem_create(int kind, int n, double lo, double hi, double omega, const void* eps, const void* mu,
+                              void* stream, vie_problem** out) {
+  g_last_error.clear();
+  if (!out) {
+    set_error("out is NULL");
+    return VIE_EINVAL;
+  }
+  *out = nullptr;
+  if (kind < VIE_LAPLACE || kind > VIE_MAXWELL) {
+    set_error("unknown kind");
+    return VIE_EINVAL;
+  }
+  if (!smooth_size(n)) {
+    set_error("n must be 2^a 3^b with 4 <= n <= 256");
+    return VIE_EINVAL;
+  }
+  if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi)) {
+    set_error("box must satisfy lo < hi");
+    return VIE_EINVAL;
+  }
+  if (!(omega >= 0.0) || !std::isfinite(omega)) {
+    set_error("omega must be finite and >= 0");
+    return VIE_EINVAL;
+  }
+  if (kind != VIE_LAPLACE && omega == 0.0) {
+    set_error("Helmholtz/Maxwell need omega > 0 (use a tiny omega for the quasi-static limit)");
+    return VIE_EINVAL;
+  }
+  if (!eps) {
+    set_error("eps is NULL");
+    return VIE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  vie_problem* P = new vie_problem();
+  P->kind = kind;
+  P->n = n;
+  P->has_mu = (kind == VIE_MAXWELL && mu != nullptr) ? 1 : 0;
+  P->ncomp = P->has_mu ? 6 : 3;
+  P->lo = lo;
+  P->hi = hi;
+  P->D = hi - lo;
+  P->h = P->D / n;
+  P->L = std::sqrt(3.0) * P->D;
+  P->omega = kind == VIE_LAPLACE ? 0.0 : omega;
+  cudaGetDevice(&P->device);
+  if (!make_plan(2 * n, &P->plan2n)) {
+    delete P;
+    set_error("bad FFT size");
+    return VIE_EINVAL;
+  }
+  vie_status s = VIE_OK;
+  cudaError_t e = cudaMalloc(&P->dflag, sizeof(int) * 4);
+  if (e != cudaSuccess) s = cuda_fail(e, "cudaMalloc(flag)");
+  if (s == VIE_OK) s = make_twiddles(2 * n, &P->tw64, &P->tw32, st);
+  if (s == VIE_OK) s = build_medium(P, eps, mu, st);
+  if (s == VIE_OK) s = build_kernels(P, st);
+  if (s == VIE_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "vie_problem_create");
+  }
+  if (s != VIE_OK) {
+    free_problem(P);
+    return s;
+  }
+  *out = P;
+  return VIE_OK;
+}
+
+int vie_problem_ncomp(const vie_problem* P) { return P ? P->ncomp : 0; }
+
+vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream) {
+  if (!P || !x || !y || nrhs < 1 || (precision != VIE_FP64 && precision != VIE_FP32)) {
+    set_error("vie_apply: bad argument");
+    return VIE_EINVAL;
+  }
+  if (x == y) {
+    set_error("vie_apply: x and y must not overlap");
+    return VIE_EINVAL;
+  }
+  return run_apply(P, P->kapply, x, y, precision, nrhs, true, (cudaStream_t)stream);
+}
+
+vie_status vie_rhs_plane_wave(vie_problem* P, const double* d, const double* p, int nrhs, void* rhs_out,
+                              void* stream) {
+  if (!P || !d || !rhs_out || nrhs < 1 || (P->kind == VIE_MAXWELL && !p)) {
+    set_error("vie_rhs_plane_wave: bad argument");
+    return VIE_EINVAL;
+  }
+  return run_rhs(P, d, p, nrhs, rhs_out, (cudaStream_t)stream);
+}
+
+vie_status vie_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_opts* opt, vie_solve_info* info,
+                     void* stream) {
+  if (!P || !rhs || !J || !opt || opt->nrhs < 1 || opt->restart < 1 || opt->restart > 200 || !(opt->tol > 0) ||
+      opt->max_inner < 1 || opt->max_outer < 0 ||
+      (opt->mode == VIE_SOLVE_MIXED && !(opt->inner_tol > 0 && opt->inner_tol < 1)) ||
+      (opt->mode != VIE_SOLVE_FP64 && opt->mode != VIE_SOLVE_MIXED)) {
+    set_error("vie_solve: bad argument");
+    return VIE_EINVAL;
+  }
+  return run_solve(P, rhs, J, opt, info, (cudaStream_t)stream);
+}
+
+vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, int nrhs, void* stream) {
+  if (!P || !J || !field_out || nrhs < 1) {
+    set_error("vie_eval_scattered: bad argument");
+    return VIE_EINVAL;
+  }
+  return run_apply(P, P->keval, J, field_out, VIE_FP64, nrhs, false, (cudaStream_t)stream);
+}
+
+size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu) {
+  const size_t N = (size_t)n * n * n;
+  const size_t O3 = (size_t)(n + 1) * (n + 1) * (n + 1);
+  const int c = (kind == VIE_MAXWELL && has_mu) ? 6 : 3;
+  const int nsym = kind == VIE_MAXWELL ? 10 : 9;
+  size_t b = 144 * N * (has_mu ? 2 : 1);                        // H: 6 entries, FP64 + FP32
+  b += 16 * O3 * nsym;                                          // raw symbol octants
+  b += 24 * O3 * 18;                                            // apply + eval sets, FP64 + FP32
+  b += apply_workspace_bytes(n, c, nrhs, VIE_FP64);             // padded intermediates
+  b += (size_t)nrhs * c * N * (8 * (restart + 1) + 16 * 2 + 8);  // mixed-precision Krylov
+  return b;
+}
+
+vie_status vie_profile_begin(vie_problem* P, int cap) {
+  if (!P || cap < 1 || cap > 100000) {
+    set_error("vie_profile_begin: bad argument");
+    return VIE_EINVAL;
+  }
+  Profiler& pf = P->prof;
+  const size_t need = (size_t)cap * (kProfSlots + 1);
+  while (pf.ev.size() < need) {
+    cudaEvent_t e;
+    VIE_CK(cudaEventCreate(&e));
+    pf.ev.push_back(e);
+  }
+  pf.on = true;
+  pf.cap = cap;
+  pf.count = 0;
+  return VIE_OK;
+}
+
+vie_status vie_profile_end(vie_problem* P, double* ms, int nslots, int* count) {
+  if (!P || !ms || nslots < 0) {
+    set_error("vie_profile_end: bad argument");
+    return VIE_EINVAL;
+  }
+  Profiler& pf = P->prof;
+  VIE_CK(cudaDeviceSynchronize());
+  for (int k = 0; k < nslots; ++k) ms[k] = 0.0;
+  for (int a = 0; a < pf.count; ++a) {
+    cudaEvent_t* ev = &pf.ev[(size_t)a * (kProfSlots + 1)];
+    for (int k = 0; k < kProfSlots && k < nslots; ++k) {
+      float t = 0.f;
+      VIE_CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      ms[k] += t;
+    }
+  }
+  if (count) *count = pf.count;
+  pf.on = false;
+  pf.count = 0;
+  return VIE_OK;
+}
+
+vie_status vie_problem_destroy(vie_problem* P) {
+  free_problem(P);
+  return VIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,426 @@
+// Set-up kernels of a problem, all in FP64 on the device:
+//  * H_eps = (eps + I)^-1 (eps - I) per node (Eq. (rhodef), Lemma 1), stored as
+//    the 6 entries of the symmetric tensor in FP64 and FP32;
+//  * the transform of the truncated Green's function (Sec. 5, steps a-b),
+//    tabulated once per distinct integer |m|^2 of the oversampled frequency grid;
+//  * the discrete kernels of every Fourier symbol (1, i k_a, -k_a k_b) with the
+//    grid Nyquist cutoff (Sec. 5, step c), brought to the (2n)^3 convolution
+//    grid and stored as octants (the kernels are even or odd in each axis).
+#include <cmath>
+#include <vector>
+
+#include "vie_internal.h"
+
+namespace vie {
+
+// ---------------------------------------------------------------- twiddles
+template <typename V>
+__global__ void k_twiddle(V* tw, int M) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  double s, c;
+  sincospi(2.0 * (double)j / (double)M, &s, &c);
+  tw[j].x = c;
+  tw[j].y = -s;
+}
+
+vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st) {
+  VIE_CK(cudaMalloc(t64, sizeof(double2) * M));
+  VIE_CK(cudaMalloc(t32, sizeof(float2) * M));
+  k_twiddle<double2><<<(M + 127) / 128, 128, 0, st>>>(*t64, M);
+  k_twiddle<float2><<<(M + 127) / 128, 128, 0, st>>>(*t32, M);
+  VIE_CK(cudaGetLastError());
+  return VIE_OK;
+}
+
+// ------------------------------------------------------------ medium tensor
+// H = (A)^-1 (eps - I) = I - 2 A^-1 with A = eps + I, via the adjugate.
+__global__ void k_medium(const double2* __restrict__ eps, double2* __restrict__ H64, float2* __restrict__ H32,
+                         long long N, int realonly, int* flag) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    double2 a[3][3];
+    double mag = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double2 v = eps[(i * 3 + j) * N + p];
+        if (realonly) v.y = 0.0;
+        a[i][j] = v;
+        mag = fmax(mag, fabs(v.x) + fabs(v.y));
+      }
+    const double tol = 1e-12 * (1.0 + mag);
+    for (int i = 0; i < 3; ++i)
+      for (int j = i + 1; j < 3; ++j)
+        if (fabs(a[i][j].x - a[j][i].x) + fabs(a[i][j].y - a[j][i].y) > tol) atomicOr(flag, 1);
+    for (int i = 0; i < 3; ++i) a[i][i].x += 1.0;
+    double2 adj[3][3];
+    adj[0][0] = cmul(a[1][1], a[2][2]) - cmul(a[1][2], a[2][1]);
+    adj[0][1] = cmul(a[0][2], a[2][1]) - cmul(a[0][1], a[2][2]);
+    adj[0][2] = cmul(a[0][1], a[1][2]) - cmul(a[0][2], a[1][1]);
+    adj[1][0] = cmul(a[1][2], a[2][0]) - cmul(a[1][0], a[2][2]);
+    adj[1][1] = cmul(a[0][0], a[2][2]) - cmul(a[0][2], a[2][0]);
+    adj[1][2] = cmul(a[0][2], a[1][0]) - cmul(a[0][0], a[1][2]);
+    adj[2][0] = cmul(a[1][0], a[2][1]) - cmul(a[1][1], a[2][0]);
+    adj[2][1] = cmul(a[0][1], a[2][0]) - cmul(a[0][0], a[2][1]);
+    adj[2][2] = cmul(a[0][0], a[1][1]) - cmul(a[0][1], a[1][0]);
+    double2 det = cmul(a[0][0], adj[0][0]) + cmul(a[0][1], adj[1][0]) + cmul(a[0][2], adj[2][0]);
+    const double dd = det.x * det.x + det.y * det.y;
+    if (!(dd > 0.0) || !isfinite(dd)) {
+      atomicOr(flag, 2);
+      continue;
+    }
+    // 1/det = conj(det)/|det|^2
+    const double2 inv = make_double2(det.x / dd, -det.y / dd);
+    const int ii[6] = {0, 1, 2, 0, 0, 1};
+    const int jj[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+      double2 q = cmul(adj[ii[e]][jj[e]], inv);
+      double2 h = make_double2(-2.0 * q.x, -2.0 * q.y);
+      if (ii[e] == jj[e]) h.x += 1.0;
+      H64[e * N + p] = h;
+      H32[e * N + p] = make_float2((float)h.x, (float)h.y);
+    }
+  }
+}
+
+vie_status build_medium(vie_problem* P, const void* eps, const void* mu, cudaStream_t st) {
+  const long long N = (long long)P->n * P->n * P->n;
+  VIE_CK(cudaMalloc(&P->He64, sizeof(double2) * 6 * N));
+  VIE_CK(cudaMalloc(&P->He32, sizeof(float2) * 6 * N));
+  VIE_CK(cudaMemsetAsync(P->dflag, 0, sizeof(int), st));
+  const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
+  k_medium<<<blocks, 256, 0, st>>>((const double2*)eps, P->He64, P->He32, N, P->kind == VIE_LAPLACE, P->dflag);
+  VIE_CK(cudaGetLastError());
+  if (P->has_mu) {
+    VIE_CK(cudaMalloc(&P->Hm64, sizeof(double2) * 6 * N));
+    VIE_CK(cudaMalloc(&P->Hm32, sizeof(float2) * 6 * N));
+    k_medium<<<blocks, 256, 0, st>>>((const double2*)mu, P->Hm64, P->Hm32, N, 0, P->dflag);
+    VIE_CK(cudaGetLastError());
+  }
+  int flag = 0;
+  VIE_CK(cudaMemcpyAsync(&flag, P->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VIE_CK(cudaStreamSynchronize(st));
+  if (flag & 1) {
+    set_error("eps/mu must be symmetric at every node");
+    return VIE_EINVAL;
+  }
+  if (flag & 2) {
+    set_error("eps + I (or mu + I) is singular or non-finite at some node");
+    return VIE_EINVAL;
+  }
+  return VIE_OK;
+}
+
+// ------------------------------------------------ truncated kernel transform
+// G^_L(kappa) = (1/kappa) int_0^L sin(kappa r) e^{i w r} dr (Sec. 5, steps a-b),
+// evaluated as [E(w + kappa) - E(w - kappa)] / (2 i kappa) with
+// E(a) = int_0^L e^{i a r} dr = L e^{i a L/2} sinc(a L/2): no cancellation at
+// kappa = w.  kappa = 0: int_0^L r e^{i w r} dr, closed form for wL >= 1/2,
+// power series sum_q (i w L)^q L^2 / (q! (q + 2)) below.  On the grids used
+// here every other kappa has kappa L >= 2 pi sqrt(3)/3, far from the
+// cancellation of the E difference at small kappa L.
+__device__ double2 dev_E(double a, double L) {
+  const double t = 0.5 * a * L;
+  const double sc = (t == 0.0) ? 1.0 : sin(t) / t;
+  double s, c;
+  sincos(t, &s, &c);
+  return make_double2(L * c * sc, L * s * sc);
+}
+
+__device__ double2 dev_ghat(double kappa, double w, double L) {
+  if (kappa == 0.0) {
+    const double wl = w * L;
+    if (fabs(wl) < 0.5) {
+      double2 acc = make_double2(0.0, 0.0);
+      double2 term = make_double2(1.0, 0.0);  // (i w L)^q / q!
+      for (int q = 0; q < 40; ++q) {
+        const double f = L * L / (double)(q + 2);
+        acc = acc + f * term;
+        term = cmul(term, make_double2(0.0, wl / (double)(q + 1)));
+      }
+      return acc;
+    }
+    double s, c;
+    sincos(wl, &s, &c);
+    return make_double2((c + s * wl - 1.0) / (w * w), (s - c * wl) / (w * w));
+  }
+  const double2 d = dev_E(w + kappa, L) - dev_E(w - kappa, L);
+  return make_double2(d.y / (2.0 * kappa), -d.x / (2.0 * kappa));
+}
+
+__global__ void k_ghat_table(double2* tab, int jmax, double dk, double w, double L) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > jmax) return;
+  tab[j] = dev_ghat(dk * sqrt((double)j), w, L);
+}
+
+// F(m) = S~(k_m) G^(|k_m|) on the (sn)^3 grid in FFT order; Nyquist rule: on an
+// axis with m_a = -sn/2 an odd factor k_a is replaced by 0 (the mean of its
+// values at -pi/h and +pi/h), an even factor k_a^2 is kept.
+__global__ void k_build_F(double2* __restrict__ F, const double2* __restrict__ tab, int sn, int sym, double dk) {
+  const long long tot = (long long)sn * sn * sn;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(idx % sn);
+    const int iy = (int)((idx / sn) % sn);
+    const int iz = (int)(idx / ((long long)sn * sn));
+    const int h = sn / 2;
+    const int mx = ix < h ? ix : ix - sn, my = iy < h ? iy : iy - sn, mz = iz < h ? iz : iz - sn;
+    const long long j = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+    const double2 G = tab[j];
+    const double kx = dk * mx, ky = dk * my, kz = dk * mz;
+    const double ox = (ix == h) ? 0.0 : kx, oy = (iy == h) ? 0.0 : ky, oz = (iz == h) ? 0.0 : kz;
+    double2 v;
+    switch (sym) {
+      case SYM_1: v = G; break;
+      case SYM_DX: v = make_double2(-ox * G.y, ox * G.x); break;
+      case SYM_DY: v = make_double2(-oy * G.y, oy * G.x); break;
+      case SYM_DZ: v = make_double2(-oz * G.y, oz * G.x); break;
+      case SYM_XX: v = (-kx * kx) * G; break;
+      case SYM_YY: v = (-ky * ky) * G; break;
+      case SYM_ZZ: v = (-kz * kz) * G; break;
+      case SYM_XY: v = (-ox * oy) * G; break;
+      case SYM_XZ: v = (-ox * oz) * G; break;
+      default: v = (-oy * oz) * G; break;
+    }
+    F[idx] = v;
+  }
+}
+
+// Generic in-place FFT of a cubic M^3 FP64 array along one axis (0 x, 1 y, 2 z).
+template <int S>
+__global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan pl, const double2* __restrict__ twg,
+                           int nl) {
+  extern __shared__ double2 sm[];
+  const int LS = M + 1;
+  double2* tw = sm;
+  double2* b0 = tw + M;
+  double2* b1 = b0 + nl * LS;
+  const int tid = flat_tid(), nt = flat_nthreads();
+  for (int j = tid; j < M; j += nt) tw[j] = twg[j];
+  const long long MM = (long long)M * M;
+  // address of element j of tile line l
+  auto addr = [&](int l, int j) -> long long {
+    if (axis == 0) return ((long long)blockIdx.x * nl + l) * M + j;
+    if (axis == 1) return (long long)blockIdx.y * MM + (long long)j * M + (long long)blockIdx.x * nl + l;
+    return (long long)j * MM + (long long)blockIdx.y * M + (long long)blockIdx.x * nl + l;
+  };
+  for (int idx = tid; idx < nl * M; idx += nt) {
+    int l, j;
+    if (axis == 0) { l = idx / M; j = idx - l * M; } else { j = idx / nl; l = idx - j * nl; }
+    b0[l * LS + j] = data[addr(l, j)];
+  }
+  __syncthreads();
+  double2* r = tile_fft<S, double>(b0, b1, pl, tw, nl, LS);
+  for (int idx = tid; idx < nl * M; idx += nt) {
+    int l, j;
+    if (axis == 0) { l = idx / M; j = idx - l * M; } else { j = idx / nl; l = idx - j * nl; }
+    data[addr(l, j)] = r[l * LS + j];
+  }
+}
+
+static int pick_nl(int M) {
+  int nl = 8;
+  while (nl > 1 && (M % nl != 0)) nl >>= 1;
+  return nl;
+}
+
+template <int S>
+static vie_status fft_cube(double2* data, int M, const FftPlan& pl, const double2* tw, cudaStream_t st) {
+  const int nl = pick_nl(M);
+  const size_t smem = sizeof(double2) * (M + 2 * nl * (M + 1));
+  VIE_CK(cudaFuncSetAttribute(k_fft_cube<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 blk(std::max(1, std::min(32, M / 16)), 1);
+  blk.y = 256 / blk.x;
+  for (int axis = 0; axis < 3; ++axis) {
+    dim3 grid = axis == 0 ? dim3((unsigned)((long long)M * M / nl), 1) : dim3(M / nl, M);
+    k_fft_cube<S><<<grid, blk, smem, st>>>(data, M, axis, pl, tw, nl);
+    VIE_CK(cudaGetLastError());
+  }
+  return VIE_OK;
+}
+
+// e[(2n)^3] from the inverse-transformed F[(sn)^3]: offsets d in [-(n-1), n-1]
+// at index d mod 2n, index n left zero; scale folds the 1/(sn)^3 of the inverse DFT.
+__global__ void k_embed(const double2* __restrict__ F, double2* __restrict__ e, int n, int sn, double scale) {
+  const int M = 2 * n;
+  const long long tot = (long long)M * M * M;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(idx % M), ey = (int)((idx / M) % M), ez = (int)(idx / ((long long)M * M));
+    if (ex == n || ey == n || ez == n) {
+      e[idx] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const int sx = ex < n ? ex : ex - M + sn;
+    const int sy = ey < n ? ey : ey - M + sn;
+    const int sz = ez < n ? ez : ez - M + sn;
+    e[idx] = scale * F[((long long)sz * sn + sy) * sn + sx];
+  }
+}
+
+__global__ void k_octant(const double2* __restrict__ E, double2* __restrict__ oct, int n) {
+  const int M = 2 * n, O = n + 1;
+  const long long tot = (long long)O * O * O;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ox = (int)(idx % O), oy = (int)((idx / O) % O), oz = (int)(idx / ((long long)O * O));
+    oct[idx] = E[((long long)oz * M + oy) * M + ox];
+  }
+}
+
+// Combine raw symbol octants into the kernel arrays of one pass.
+//   coef layout per output array a: up to 2 terms (sym index, complex factor).
+struct CombineDesc {
+  int narr;
+  int sym[9][2];
+  double2 fac[9][2];
+};
+
+__global__ void k_combine(const double2* __restrict__ sym_oct, double2* __restrict__ out64, float2* __restrict__ out32,
+                          long long O3, CombineDesc cd, double diag_add_scale, int diag_mask) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < O3;
+       idx += (long long)gridDim.x * blockDim.x) {
+    for (int a = 0; a < cd.narr; ++a) {
+      double2 v = make_double2(0.0, 0.0);
+      for (int t = 0; t < 2; ++t) {
+        const int s = cd.sym[a][t];
+        if (s < 0) continue;
+        v = v + cmul(cd.fac[a][t], sym_oct[(long long)s * O3 + idx]);
+      }
+      if (diag_mask & (1 << a)) v.x += diag_add_scale;
+      out64[a * O3 + idx] = v;
+      out32[a * O3 + idx] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+}
+
+static vie_status combine(vie_problem* P, KernelSet& K, int mode, const CombineDesc& cd, double diag_add,
+                          int diag_mask, cudaStream_t st) {
+  const long long O = P->n + 1, O3 = O * O * O;
+  K.mode = mode;
+  K.narr = cd.narr;
+  VIE_CK(cudaMalloc(&K.oct64, sizeof(double2) * cd.narr * O3));
+  VIE_CK(cudaMalloc(&K.oct32, sizeof(float2) * cd.narr * O3));
+  const int blocks = (int)std::min<long long>((O3 + 255) / 256, 152LL * 16);
+  k_combine<<<blocks, 256, 0, st>>>(P->sym_oct, K.oct64, K.oct32, O3, cd, diag_add, diag_mask);
+  VIE_CK(cudaGetLastError());
+  return VIE_OK;
+}
+
+vie_status build_kernels(vie_problem* P, cudaStream_t st) {
+  const int n = P->n, sn = 3 * n, M = 2 * n;
+  const double dk = 2.0 * M_PI / (3.0 * P->D);
+  const int jmax = 3 * (sn / 2) * (sn / 2);
+  const double w = P->kind == VIE_LAPLACE ? 0.0 : P->omega;
+  double2* tab = nullptr;
+  double2 *F = nullptr, *E = nullptr, *tw_sn = nullptr;
+  float2* tw_sn32 = nullptr;
+  VIE_CK(cudaMalloc(&tab, sizeof(double2) * (jmax + 1)));
+  k_ghat_table<<<(jmax + 256) / 256, 256, 0, st>>>(tab, jmax, dk, w, P->L);
+  VIE_CK(cudaGetLastError());
+  const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = (long long)(n + 1) * (n + 1) * (n + 1);
+  VIE_CK(cudaMalloc(&F, sizeof(double2) * S3));
+  VIE_CK(cudaMalloc(&E, sizeof(double2) * M3));
+  vie_status s = make_twiddles(sn, &tw_sn, &tw_sn32, st);
+  if (s != VIE_OK) return s;
+  FftPlan plsn;
+  if (!make_plan(sn, &plsn)) {
+    set_error("bad oversampled grid size");
+    return VIE_EINVAL;
+  }
+  VIE_CK(cudaMalloc(&P->sym_oct, sizeof(double2) * SYM_COUNT * O3));
+  const bool need1 = P->kind == VIE_MAXWELL;
+  const int gb = 152 * 16;
+  for (int sym = 0; sym < SYM_COUNT; ++sym) {
+    if (sym == SYM_1 && !need1) continue;
+    k_build_F<<<gb, 256, 0, st>>>(F, tab, sn, sym, dk);
+    VIE_CK(cudaGetLastError());
+    s = fft_cube<+1>(F, sn, plsn, tw_sn, st);
+    if (s != VIE_OK) return s;
+    k_embed<<<gb, 256, 0, st>>>(F, E, n, sn, 1.0 / (double)S3);
+    VIE_CK(cudaGetLastError());
+    s = fft_cube<-1>(E, M, P->plan2n, P->tw64, st);
+    if (s != VIE_OK) return s;
+    k_octant<<<gb, 256, 0, st>>>(E, P->sym_oct + (long long)sym * O3, n);
+    VIE_CK(cudaGetLastError());
+  }
+  VIE_CK(cudaStreamSynchronize(st));
+  cudaFree(F);
+  cudaFree(E);
+  cudaFree(tab);
+  cudaFree(tw_sn);
+  cudaFree(tw_sn32);
+
+  // Fold constants: apply kernels give u with y = x + H u; the 1/(2n)^3 of the
+  // inverse DFT is folded in too.
+  const double nrm = 1.0 / (double)M3;
+  const int Q[6] = {SYM_XX, SYM_YY, SYM_ZZ, SYM_XY, SYM_XZ, SYM_YZ};
+  const int Dd[3] = {SYM_DX, SYM_DY, SYM_DZ};
+  CombineDesc ca{}, ce{};
+  for (int a = 0; a < 9; ++a)
+    for (int t = 0; t < 2; ++t) {
+      ca.sym[a][t] = -1;
+      ce.sym[a][t] = -1;
+      ca.fac[a][t] = make_double2(0, 0);
+      ce.fac[a][t] = make_double2(0, 0);
+    }
+  const double w2 = w * w;
+  if (P->kind == VIE_LAPLACE || P->kind == VIE_HELMHOLTZ) {
+    // Laplace  (Eq. (eq:intLap)):  u = -2 T_0 x  (y = x + H_eps u)
+    // Helmholtz (Eq. (eq:intH), H_{eps^-1} = -H_eps): u = +2 T_w x
+    const double sg = P->kind == VIE_LAPLACE ? -2.0 : 2.0;
+    ca.narr = 6;
+    for (int a = 0; a < 6; ++a) {
+      ca.sym[a][0] = Q[a];
+      ca.fac[a][0] = make_double2(sg * nrm, 0);
+    }
+    s = combine(P, P->kapply, KM_SYM3, ca, sg * 0.5 * nrm, 0x7, st);
+    if (s != VIE_OK) return s;
+    // phi_sc = div V J
+    ce.narr = 3;
+    for (int a = 0; a < 3; ++a) {
+      ce.sym[a][0] = Dd[a];
+      ce.fac[a][0] = make_double2(nrm, 0);
+    }
+    s = combine(P, P->keval, KM_DIV, ce, 0.0, 0, st);
+    if (s != VIE_OK) return s;
+  } else {
+    // Maxwell (Eq. (eq:intM)): u_J = Q' J + P' x M, u_M = Q' M - P' x J with
+    // Q' = -2 (K + I/2 + w^2 V), P'_a = -2 i w K_{i k_a}.
+    ca.narr = P->has_mu ? 9 : 6;
+    for (int a = 0; a < 6; ++a) {
+      ca.sym[a][0] = Q[a];
+      ca.fac[a][0] = make_double2(-2.0 * nrm, 0);
+      if (a < 3) {
+        ca.sym[a][1] = SYM_1;
+        ca.fac[a][1] = make_double2(-2.0 * w2 * nrm, 0);
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      ca.sym[6 + a][0] = Dd[a];
+      ca.fac[6 + a][0] = make_double2(0, -2.0 * w * nrm);
+    }
+    s = combine(P, P->kapply, P->has_mu ? KM_MAXWELL6 : KM_SYM3, ca, -nrm, 0x7, st);
+    if (s != VIE_OK) return s;
+    // E_sc = Q'' J + P'' x M, H_sc = Q'' M - P'' x J; Q'' = K + w^2 V, P''_a = i w K_{i k_a}
+    ce.narr = 9;
+    for (int a = 0; a < 6; ++a) {
+      ce.sym[a][0] = Q[a];
+      ce.fac[a][0] = make_double2(nrm, 0);
+      if (a < 3) {
+        ce.sym[a][1] = SYM_1;
+        ce.fac[a][1] = make_double2(w2 * nrm, 0);
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      ce.sym[6 + a][0] = Dd[a];
+      ce.fac[6 + a][0] = make_double2(0, w * nrm);
+    }
+    s = combine(P, P->keval, P->has_mu ? KM_MAXWELL6 : KM_EMRED, ce, 0.0, 0, st);
+    if (s != VIE_OK) return s;
+  }
+  VIE_CK(cudaStreamSynchronize(st));
+  return VIE_OK;
+}
+
+}  // namespace vie

@@ -1,0 +1,246 @@
+// Device-side building blocks shared by every kernel of the library:
+// complex arithmetic on CUDA vector types, small DFT codelets, and a
+// shared-memory mixed-radix (2, 3, 4, 8, 16) Stockham FFT that transforms a
+// tile of lines resident in shared memory.
+//
+// The FFT is the engine of the truncated-kernel method of Sec. 5 (steps a-c:
+// truncate the Green's function, transform it, cut off at the grid Nyquist
+// frequency); every volume potential is applied as a zero-padded circular
+// convolution on a (2n)^3 grid.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace vie {
+
+// ------------------------------------------------------------ complex math
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+template <typename T> struct CT;
+template <> struct CT<double> {
+  typedef double2 V;
+  static __host__ __device__ __forceinline__ V make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct CT<float> {
+  typedef float2 V;
+  static __host__ __device__ __forceinline__ V make(float a, float b) { return make_float2(a, b); }
+};
+
+// a * (S i) for S = +1 / -1
+template <int S, typename V>
+__device__ __forceinline__ V mul_si(V a) {
+  V r;
+  if (S > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
+// ------------------------------------------------------------ codelets
+// In-place DFT of length R on registers: U_q = sum_r u_r exp(S 2 pi i r q / R).
+template <int R, int S, typename T> struct Dft;
+
+template <int S, typename T> struct Dft<2, S, T> {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    V t = u[0];
+    u[0] = t + u[1];
+    u[1] = t - u[1];
+  }
+};
+
+template <int S, typename T> struct Dft<3, S, T> {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    const T h3 = (T)0.86602540378443864676;  // sqrt(3)/2
+    V t = u[1] + u[2];
+    V m = u[0] - (T)0.5 * t;
+    V d = mul_si<S>(h3 * (u[1] - u[2]));
+    u[0] = u[0] + t;
+    u[1] = m + d;
+    u[2] = m - d;
+  }
+};
+
+template <int S, typename T> struct Dft<4, S, T> {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    V a0 = u[0] + u[2], a1 = u[0] - u[2];
+    V b0 = u[1] + u[3], b1 = mul_si<S>(u[1] - u[3]);
+    u[0] = a0 + b0;
+    u[2] = a0 - b0;
+    u[1] = a1 + b1;
+    u[3] = a1 - b1;
+  }
+};
+
+template <int S, typename T> struct Dft<8, S, T> {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    const T r2 = (T)0.70710678118654752440;
+    V e[4] = {u[0], u[2], u[4], u[6]};
+    V o[4] = {u[1], u[3], u[5], u[7]};
+    Dft<4, S, T>::run(e);
+    Dft<4, S, T>::run(o);
+    // w8^q = exp(S 2 pi i q / 8)
+    V o1 = CT<T>::make(r2 * (o[1].x - (T)S * o[1].y), r2 * (o[1].y + (T)S * o[1].x));  // (1 + S i)/sqrt2
+    V o2 = mul_si<S>(o[2]);
+    V o3 = CT<T>::make(r2 * (-o[3].x - (T)S * o[3].y), r2 * (-o[3].y + (T)S * o[3].x));  // (-1 + S i)/sqrt2
+    u[0] = e[0] + o[0];
+    u[4] = e[0] - o[0];
+    u[1] = e[1] + o1;
+    u[5] = e[1] - o1;
+    u[2] = e[2] + o2;
+    u[6] = e[2] - o2;
+    u[3] = e[3] + o3;
+    u[7] = e[3] - o3;
+  }
+};
+
+// cos(pi j / 8), j = 0..15
+__device__ __forceinline__ double cos_pi8(int j) {
+  const double c[16] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                        0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                        -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173,
+                        0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613};
+  return c[j & 15];
+}
+
+template <int S, typename T> struct Dft<16, S, T> {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    // r = 4 r1 + r2, q = q1 + 4 q2
+    V a[4][4];
+#pragma unroll
+    for (int r2 = 0; r2 < 4; ++r2) {
+      V t[4] = {u[r2], u[4 + r2], u[8 + r2], u[12 + r2]};
+      Dft<4, S, T>::run(t);
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1) {
+        const int j = r2 * q1;  // w16^(r2 q1)
+        if (j == 0) {
+          a[q1][r2] = t[q1];
+        } else {
+          const T c = (T)cos_pi8(j);
+          const T s = (T)S * (T)cos_pi8(j + 12);  // sin(pi j/8) = cos(pi (j - 4)/8) = cos(pi (j+12)/8)
+          a[q1][r2] = CT<T>::make(c * t[q1].x - s * t[q1].y, c * t[q1].y + s * t[q1].x);
+        }
+      }
+    }
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) {
+      Dft<4, S, T>::run(a[q1]);
+#pragma unroll
+      for (int q2 = 0; q2 < 4; ++q2) u[q1 + 4 * q2] = a[q1][q2];
+    }
+  }
+};
+
+// ------------------------------------------------------------ FFT plan
+struct FftPlan {
+  int M;      // transform length
+  int ns;     // number of stages
+  int R[8];   // radices, first stage first
+};
+
+// Factor M = 2^a 3^b into radices 16, 8, 4, 2 and 3; returns false if M has other factors.
+inline bool make_plan(int M, FftPlan* pl) {
+  pl->M = M;
+  pl->ns = 0;
+  int m = M;
+  const int rad[4] = {16, 8, 4, 2};
+  for (int k = 0; k < 4; ++k)
+    while (m % rad[k] == 0 && m > 1) {
+      if (pl->ns >= 8) return false;
+      pl->R[pl->ns++] = rad[k];
+      m /= rad[k];
+    }
+  while (m % 3 == 0) {
+    if (pl->ns >= 8) return false;
+    pl->R[pl->ns++] = 3;
+    m /= 3;
+  }
+  return m == 1 && M >= 2;
+}
+
+// One Stockham stage of radix R over nl lines of length M stored at stride ls.
+// Butterfly i of a line reads in[i + r M/R] (r < R), twiddles by
+// exp(S 2 pi i r k / (p R)) with k = i mod p, and writes out[(i - k) R + k + r p].
+// tw[j] = exp(-2 pi i j / M).  Thread layout: blockDim = (TX, TY).
+template <int R, int S, typename T>
+__device__ __forceinline__ void stage(const typename CT<T>::V* __restrict__ in, typename CT<T>::V* __restrict__ out,
+                                      int M, int p, const typename CT<T>::V* __restrict__ tw, int nl, int ls) {
+  typedef typename CT<T>::V V;
+  const int nb = M / R;
+  const int step = M / (p * R);
+  for (int l = threadIdx.y; l < nl; l += blockDim.y) {
+    const V* src = in + l * ls;
+    V* dst = out + l * ls;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const int k = i % p;
+      V u[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r] = src[i + r * nb];
+      if (k != 0) {
+        const int st = k * step;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          V w = tw[r * st];
+          u[r] = (S < 0) ? cmul(u[r], w) : cmulc(u[r], w);
+        }
+      }
+      Dft<R, S, T>::run(u);
+      const int j = (i - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[j + r * p] = u[r];
+    }
+  }
+}
+
+// Transform nl lines held in buffer a (stride ls) in place-of-ping-pong with b.
+// Must be called by every thread of the block after the data is in a and
+// synchronised.  Returns the buffer that holds the result (synchronised).
+template <int S, typename T>
+__device__ typename CT<T>::V* tile_fft(typename CT<T>::V* a, typename CT<T>::V* b, const FftPlan& pl,
+                                       const typename CT<T>::V* tw, int nl, int ls) {
+  int p = 1;
+  for (int s = 0; s < pl.ns; ++s) {
+    const int R = pl.R[s];
+    switch (R) {
+      case 16: stage<16, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 8: stage<8, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 4: stage<4, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 2: stage<2, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      default: stage<3, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+    }
+    __syncthreads();
+    typename CT<T>::V* t = a;
+    a = b;
+    b = t;
+    p *= R;
+  }
+  return a;
+}
+
+__device__ __forceinline__ int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int flat_nthreads() { return blockDim.x * blockDim.y; }
+
+}  // namespace vie

@@ -1,0 +1,120 @@
+// Internal state of a problem handle and host-side helpers shared by the
+// translation units of the library.  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vie.h"
+#include "vie_fft.cuh"
+
+namespace vie {
+
+// Symbols of the discrete kernels (Fourier multipliers of the truncated
+// Green's function): 1, i k_a, -k_a k_b.
+enum Sym { SYM_1 = 0, SYM_DX, SYM_DY, SYM_DZ, SYM_XX, SYM_YY, SYM_ZZ, SYM_XY, SYM_XZ, SYM_YZ, SYM_COUNT };
+
+// Which kernel-array set a convolution pass uses (how the k-space mixing works).
+enum KMode {
+  KM_SYM3 = 0,     // 3 -> 3, symmetric 3x3 (6 arrays: xx yy zz xy xz yz)
+  KM_MAXWELL6 = 1, // 6 -> 6: [Q J + P x M ; Q M - P x J] (6 Q arrays + 3 P arrays)
+  KM_DIV = 2,      // 3 -> 1: sum_a G_a J_a (3 arrays)
+  KM_EMRED = 3,    // 3 -> 6: [Q J ; -P x J] (6 Q arrays + 3 P arrays)
+};
+
+// Per-array parity on the (2n)^3 grid: bit a set = odd under k_a -> -k_a (a = 0 x, 1 y, 2 z).
+// Order of the arrays in a set: Q (xx yy zz xy xz yz) then P (x y z).
+__host__ __device__ __forceinline__ int sym_parity(int a) {
+  switch (a) {
+    case 3: return 1 | 2;
+    case 4: return 1 | 4;
+    case 5: return 2 | 4;
+    case 6: return 1;
+    case 7: return 2;
+    case 8: return 4;
+    default: return 0;
+  }
+}
+
+struct KernelSet {
+  int mode = 0;
+  int narr = 0;                 // 3, 6 or 9
+  double2* oct64 = nullptr;     // [narr][(n+1)^3] FP64
+  float2* oct32 = nullptr;      // [narr][(n+1)^3] FP32
+};
+
+struct Workspace {
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+
+// Optional per-kernel event timing of the apply pipeline (vie_profile_*).
+static const int kProfSlots = 5;
+struct Profiler {
+  bool on = false;
+  int cap = 0;
+  int count = 0;
+  std::vector<cudaEvent_t> ev;  // (kProfSlots + 1) events per recorded apply
+};
+
+}  // namespace vie
+
+struct vie_problem {
+  int kind = 0;
+  int n = 0;
+  int ncomp = 3;   // unknown components: 3, or 6 for Maxwell with mu
+  int has_mu = 0;
+  double lo = 0, hi = 0, D = 0, h = 0, L = 0, omega = 0;
+  int device = 0;
+  vie::FftPlan plan2n;
+  double2* tw64 = nullptr;   // exp(-2 pi i j / 2n), j < 2n
+  float2* tw32 = nullptr;
+  double2* He64 = nullptr;   // [6][n^3] symmetric H_eps (xx yy zz xy xz yz)
+  float2* He32 = nullptr;
+  double2* Hm64 = nullptr;   // [6][n^3] H_mu (Maxwell with mu)
+  float2* Hm32 = nullptr;
+  double2* sym_oct = nullptr;  // [SYM_COUNT][(n+1)^3] raw symbol kernels DFT_{2n}, FP64
+  vie::KernelSet kapply;     // operator kernels (with I/2, 2H sign and 1/(2n)^3 folded in)
+  vie::KernelSet keval;      // scattered-field kernels
+  vie::Workspace ws;         // padded intermediates
+  vie::Workspace ks;         // Krylov workspace
+  vie::Profiler prof;
+  int* dflag = nullptr;      // device error flag (NaN, bad input)
+};
+
+namespace vie {
+
+void set_error(const std::string& msg);
+vie_status cuda_fail(cudaError_t e, const char* what);
+
+#define VIE_CK(call)                                               \
+  do {                                                             \
+    cudaError_t _e = (call);                                       \
+    if (_e != cudaSuccess) return ::vie::cuda_fail(_e, #call);     \
+  } while (0)
+
+// precompute.cu
+vie_status build_medium(vie_problem* P, const void* eps, const void* mu, cudaStream_t st);
+vie_status build_kernels(vie_problem* P, cudaStream_t st);
+vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st);
+
+// apply.cu
+// Convolution pipeline: out = epilogue(K * pad(in)).  prec 0 = FP64, 1 = FP32.
+// in/out layout [nrhs][c][n][n][n] complex.  If with_identity, out = in + H u
+// (u = the convolution); otherwise out = u.
+vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
+                     bool with_identity, cudaStream_t st);
+size_t apply_workspace_bytes(int n, int c, int nrhs, int prec);
+
+// krylov.cu
+vie_status run_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_opts* opt, vie_solve_info* info,
+                     cudaStream_t st);
+vie_status run_rhs(vie_problem* P, const double* d, const double* p, int nrhs, void* out, cudaStream_t st);
+
+inline int cin_of(int mode) { return mode == KM_MAXWELL6 ? 6 : 3; }
+inline int cout_of(int mode) { return mode == KM_SYM3 ? 3 : (mode == KM_DIV ? 1 : 6); }
+
+}  // namespace vie

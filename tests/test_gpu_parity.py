@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative L2 over all components):
+* FP64 apply / rhs / scattered field: 1e-12 (both sides compute the same
+  discrete convolution in FP64; they differ only in rounding order).
+* FP32 apply: 2e-5.  Each FFT stage adds ~eps_32 = 6e-8 relative error; a
+  pruned forward plus inverse 3D transform on (2n)^3 has 2 log2((2n)^3) ~ 50
+  butterfly levels at 2n = 256, i.e. ~3e-6 -- the tolerance leaves a 6x margin.
+* FP64 solve: 1e-10 (spec bound for FP64 paths); mixed solve: 1e-6 after
+  refinement (spec bound), tested here at a tighter 1e-8.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import vie_inputs as vi
+from oracle import operators, solvers
+
+from gpu_common import eps_dev, mu_dev, rel, to_dev, vie  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("laplace", 8, 0.0, False),
+    ("laplace", 12, 0.0, False),
+    ("laplace", 32, 0.0, False),
+    ("helmholtz", 8, 2.0, False),
+    ("helmholtz", 24, 4.0, False),
+    ("maxwell", 8, 1.5, False),
+    ("maxwell", 12, 2.0, True),
+    ("maxwell", 16, 3.0, True),
+]
+
+
+def make_problem(kind, n, wavelengths, with_mu, seed=0):
+    if kind == "laplace":
+        return vi.laplace_bump_problem(n=n, seed=seed)
+    if kind == "helmholtz":
+        return vi.helmholtz_problem(n=n, wavelengths=wavelengths, seed=seed)
+    return vi.maxwell_problem(n=n, wavelengths=wavelengths, with_mu=with_mu, seed=seed)
+
+
+_cache = {}
+
+
+def setup(vie, kind, n, wl, with_mu):
+    key = (kind, n, wl, with_mu)
+    if key not in _cache:
+        p = make_problem(kind, n, wl, with_mu)
+        P = vie.Problem(kind, n, p.lo, p.hi, p.omega, eps_dev(p), mu_dev(p))
+        op = operators.OracleProblem.from_problem(p)
+        _cache[key] = (p, P, op)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}-mu{int(c[3])}")
+def test_apply_fp64(vie, case):
+    import torch
+
+    p, P, op = setup(vie, *case)
+    x = vi.random_field(p.n, op.ncomp, 1)[0]
+    xd = to_dev(x)
+    yd = torch.empty_like(xd)
+    P.apply(xd, yd, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    assert rel(yd.cpu().numpy(), op.apply(x)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}-mu{int(c[3])}")
+def test_apply_fp32(vie, case):
+    import torch
+
+    p, P, op = setup(vie, *case)
+    x = vi.random_field(p.n, op.ncomp, 2)[0]
+    xd = to_dev(x, torch.complex64)
+    yd = torch.empty_like(xd)
+    P.apply(xd, yd, vie.VIE_FP32)
+    torch.cuda.synchronize()
+    assert rel(yd.cpu().numpy(), op.apply(x.astype(np.complex64).astype(np.complex128))) <= 2e-5
+
+
+def test_apply_batched_equals_single(vie):
+    import torch
+
+    p, P, op = setup(vie, "helmholtz", 24, 4.0, False)
+    x = vi.random_field(p.n, 3, 3, nrhs=3)
+    xd = to_dev(x)
+    yb = torch.empty_like(xd)
+    P.apply(xd, yb, vie.VIE_FP64, nrhs=3)
+    for r in range(3):
+        ys = torch.empty_like(xd[r])
+        P.apply(xd[r].contiguous(), ys, vie.VIE_FP64)
+        torch.cuda.synchronize()
+        assert torch.equal(ys, yb[r])
+
+
+@pytest.mark.parametrize("case", CASES[::2] + [CASES[6]], ids=lambda c: f"{c[0]}-{c[1]}-mu{int(c[3])}")
+def test_rhs(vie, case):
+    import torch
+
+    p, P, op = setup(vie, *case)
+    out = torch.empty((op.ncomp, p.n, p.n, p.n), dtype=torch.complex128, device="cuda:0")
+    d = p.directions[0]
+    pol = p.polarisations[0] if p.kind == "maxwell" else None
+    P.rhs(d, pol, 1, out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), op.rhs(d, pol)) <= 1e-13
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}-mu{int(c[3])}")
+def test_scattered_field(vie, case):
+    import torch
+
+    p, P, op = setup(vie, *case)
+    x = vi.random_field(p.n, op.ncomp, 4)[0]
+    cout = 1 if p.kind != "maxwell" else 6
+    out = torch.empty((cout, p.n, p.n, p.n), dtype=torch.complex128, device="cuda:0")
+    P.eval_scattered(to_dev(x), out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), op.scattered(x)) <= 1e-12
+
+
+def test_solve_fp64_laplace_32(vie):
+    """Config-1 workload: anisotropic Laplace bump, 32^3, GMRES to 1e-10 (FP64)."""
+    import torch
+
+    p, P, op = setup(vie, "laplace", 32, 0.0, False)
+    b = torch.empty((3, 32, 32, 32), dtype=torch.complex128, device="cuda:0")
+    P.rhs(p.directions[0], None, 1, b)
+    J = torch.zeros_like(b)
+    st, info = P.solve(b, J, tol=1e-12, restart=50, mode=vie.VIE_SOLVE_FP64)
+    Jo, io = solvers.gmres(op.apply, op.rhs(p.directions[0]), tol=1e-13, restart=50)
+    assert info.rel_residual <= 1e-12
+    assert rel(J.cpu().numpy(), Jo) <= 1e-10
+
+
+def test_solve_fp64_laplace_dense_8(vie):
+    import torch
+
+    p, P, op = setup(vie, "laplace", 8, 0.0, False)
+    b = torch.empty((3, 8, 8, 8), dtype=torch.complex128, device="cuda:0")
+    P.rhs(p.directions[0], None, 1, b)
+    J = torch.zeros_like(b)
+    P.solve(b, J, tol=1e-13, restart=60, mode=vie.VIE_SOLVE_FP64)
+    Jo = solvers.dense_solve(op.apply, op.rhs(p.directions[0]))
+    assert rel(J.cpu().numpy(), Jo) <= 1e-10
+
+
+@pytest.mark.parametrize("case", [CASES[4], CASES[6]], ids=lambda c: f"{c[0]}-{c[1]}-mu{int(c[3])}")
+def test_solve_mixed(vie, case):
+    import torch
+
+    p, P, op = setup(vie, *case)
+    d = p.directions[0]
+    pol = p.polarisations[0] if p.kind == "maxwell" else None
+    b = torch.empty((op.ncomp, p.n, p.n, p.n), dtype=torch.complex128, device="cuda:0")
+    P.rhs(d, pol, 1, b)
+    J = torch.zeros_like(b)
+    st, info = P.solve(b, J, tol=1e-10, restart=40, mode=vie.VIE_SOLVE_MIXED, inner_tol=1e-5, max_outer=30)
+    Jo, _ = solvers.gmres(op.apply, op.rhs(d, pol), tol=1e-13, restart=60)
+    assert info.rel_residual <= 1e-10
+    assert info.applies_fp32 > info.applies_fp64
+    assert rel(J.cpu().numpy(), Jo) <= 1e-8
+
+
+def test_solve_fp64_helmholtz_multi_rhs(vie):
+    import torch
+
+    p = vi.helmholtz_problem(n=12, wavelengths=2.0, nrhs=2, seed=4)
+    P = vie.Problem("helmholtz", 12, p.lo, p.hi, p.omega, eps_dev(p))
+    op = operators.OracleProblem.from_problem(p)
+    b = torch.empty((2, 3, 12, 12, 12), dtype=torch.complex128, device="cuda:0")
+    P.rhs(p.directions, None, 2, b)
+    J = torch.zeros_like(b)
+    st, info = P.solve(b, J, tol=1e-12, restart=30, mode=vie.VIE_SOLVE_FP64, nrhs=2)
+    for r in range(2):
+        Jo, _ = solvers.gmres(op.apply, op.rhs(p.directions[r]), tol=1e-13, restart=60)
+        assert rel(J[r].cpu().numpy(), Jo) <= 1e-10
+
+
+def test_invalid_arguments(vie):
+    import torch
+
+    p = vi.laplace_bump_problem(n=8)
+    e = eps_dev(p)
+    for bad in [dict(n=5), dict(n=7), dict(n=512), dict(lo=1.0, hi=1.0), dict(omega=-1.0)]:
+        kw = dict(kind=vie.VIE_LAPLACE, n=8, lo=-1.0, hi=1.0, omega=0.0)
+        kw.update(bad)
+        with pytest.raises(vie.VieError) as ei:
+            vie.vie_problem_create(kw["kind"], kw["n"], kw["lo"], kw["hi"], kw["omega"], e)
+        assert ei.value.status == vie.VIE_EINVAL
+    asym = p.eps.copy()
+    asym[0, 1] += 0.1
+    with pytest.raises(vie.VieError) as ei:
+        vie.vie_problem_create(vie.VIE_LAPLACE, 8, -1.0, 1.0, 0.0, to_dev(asym.reshape(9, -1)))
+    assert ei.value.status == vie.VIE_EINVAL
+    with pytest.raises(vie.VieError):
+        vie.vie_problem_create(vie.VIE_HELMHOLTZ, 8, -1.0, 1.0, 0.0, e)
+    P = vie.Problem("laplace", 8, -1.0, 1.0, 0.0, e)
+    x = torch.zeros((3, 8, 8, 8), dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(vie.VieError):
+        vie.vie_apply(P.handle, x, x, vie.VIE_FP64)
+    with pytest.raises(vie.VieError):
+        vie.vie_apply(P.handle, x, torch.empty_like(x), 7)
+
+
+def test_smallest_grid_and_zero_input(vie):
+    import torch
+
+    p = vi.laplace_bump_problem(n=4)
+    P = vie.Problem("laplace", 4, p.lo, p.hi, 0.0, eps_dev(p))
+    op = operators.OracleProblem.from_problem(p)
+    x = vi.random_field(4, 3, 9)[0]
+    y = torch.empty((3, 4, 4, 4), dtype=torch.complex128, device="cuda:0")
+    P.apply(to_dev(x), y, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), op.apply(x)) <= 1e-12
+    z = torch.zeros_like(y)
+    P.apply(z, y, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(y) == 0
+    # a zero right-hand side solves to zero without iterating
+    J = torch.ones_like(y)
+    st, info = P.solve(z, J)
+    assert torch.count_nonzero(J) == 0
+
+
+def test_low_frequency_helmholtz_equals_laplace_inverse_eps(vie):
+    """w -> 0: the Helmholtz operator with eps equals the Laplace operator with eps^-1 (GPU only)."""
+    import torch
+
+    n = 12
+    # Laplace takes Re(eps): use a lossless medium so that eps^-1 is real
+    p2 = vi.helmholtz_problem(n=n, wavelengths=1e-10, seed=2, lossless=True)
+    Ph = vie.Problem("helmholtz", n, p2.lo, p2.hi, p2.omega, eps_dev(p2))
+    Pl = vie.Problem("laplace", n, p2.lo, p2.hi, 0.0, to_dev(operators.inverse_field(p2.eps).reshape(9, -1)))
+    x = to_dev(vi.random_field(n, 3, 5)[0])
+    yh = torch.empty_like(x)
+    yl = torch.empty_like(x)
+    Ph.apply(x, yh, vie.VIE_FP64)
+    Pl.apply(x, yl, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    assert rel(yh.cpu().numpy(), yl.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.slow
+def test_full_size_helmholtz_128_fp32(vie):
+    """The workload bench.py times (Helmholtz, 128^3, FP32 apply): every output against the oracle."""
+    import torch
+
+    p = vi.helmholtz_problem(n=128, wavelengths=4.0, seed=0)
+    P = vie.Problem("helmholtz", 128, p.lo, p.hi, p.omega, eps_dev(p))
+    x = vi.random_field(128, 3, 0)[0]
+    xd = to_dev(x, torch.complex64)
+    y32 = torch.empty_like(xd)
+    P.apply(xd, y32, vie.VIE_FP32)
+    y64 = torch.empty((3, 128, 128, 128), dtype=torch.complex128, device="cuda:0")
+    P.apply(xd.to(torch.complex128), y64, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    op = operators.OracleProblem.from_problem(p)
+    yo = op.apply(x.astype(np.complex64).astype(np.complex128))
+    assert rel(y64.cpu().numpy(), yo) <= 1e-12
+    assert rel(y32.cpu().numpy(), yo) <= 2e-5
