@@ -2,12 +2,16 @@
 //
 // Sec. 1 and Sec. 6 name GMRES (and Bi-CGStab, used in Sec. 5) as the
 // iterative solvers for these second-kind equations.  Two modes:
-//  * FP64: restarted GMRES(m) on the FP64 apply; classical Gram-Schmidt with
-//    one reorthogonalisation (CGS2), Givens rotations, FP64 everywhere.
+//  * FP64: restarted GMRES(m) on the FP64 apply, FP64 everywhere.
 //  * mixed: FP64 iterative refinement r = b - A x (FP64 apply), inner GMRES(m)
-//    on the FP32 apply with an FP32 Krylov basis, inner products accumulated
-//    in FP64, Hessenberg and least squares in FP64; x += V y in FP64.
-// Vector kernels accumulate in FP64 in a fixed order (deterministic reruns).
+//    on the FP32 apply with an FP32 Krylov basis; Hessenberg matrix, Givens
+//    rotations, least squares and the iterate x in FP64.
+// Arnoldi: classical Gram-Schmidt, one device reduction per step (inner
+// products and |w|^2 in one pass, the update and |w'|^2 in a second), and a
+// second Gram-Schmidt pass only when the first removed more than 3/4 of the
+// norm.  Reductions use a fixed order (reruns are bit-identical); per-thread
+// partial sums are FP64 for an FP64 basis and FP32 for an FP32 basis, the
+// cross-thread sums always FP64.
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -94,30 +98,43 @@ __device__ __forceinline__ double2 to_d(V a) {
   return make_double2((double)a.x, (double)a.y);
 }
 
-// partial[i * G + block] = sum over this block's elements of conj(V_i) w, i < k.
-template <typename TB, typename TW>
+// Per-thread accumulation type: FP64 for an FP64 basis; FP32 for an FP32
+// basis (each thread sums only ~L / 77824 terms in FP32 before the FP64
+// cross-thread reduction -- far below the inner tolerance of the FP32 solve,
+// and it keeps the FP32 Arnoldi process off GB300's slow FP64 pipes).
+template <typename TB> struct Acc;
+template <> struct Acc<double2> { typedef double T; typedef double2 V; };
+template <> struct Acc<float2> { typedef float T; typedef float2 V; };
+
+// partial[i * G + block] = sum over this block's elements of conj(V_i) w, i < k;
+// if with_self, slot k also gets conj(w) w.
+template <typename TB>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__ Vb, long long ldv, int k,
-                                                          const TW* __restrict__ w, long long L, double2* partial) {
+                                                          const TB* __restrict__ w, long long L, double2* partial,
+                                                          int with_self) {
+  typedef typename Acc<TB>::T AT;
   __shared__ double2 red[kRedThreads / 32][kDotChunk];
   const int G = gridDim.x;
-  for (int i0 = 0; i0 < k; i0 += kDotChunk) {
-    const int cnt = min(kDotChunk, k - i0);
-    double2 acc[kDotChunk];
+  const int ktot = k + (with_self ? 1 : 0);
+  for (int i0 = 0; i0 < ktot; i0 += kDotChunk) {
+    const int cnt = min(kDotChunk, ktot - i0);
+    AT ar[kDotChunk], ai[kDotChunk];
 #pragma unroll
-    for (int t = 0; t < kDotChunk; ++t) acc[t] = make_double2(0, 0);
+    for (int t = 0; t < kDotChunk; ++t) ar[t] = ai[t] = (AT)0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)G * blockDim.x) {
-      const double2 we = to_d(w[e]);
+      const TB we = w[e];
 #pragma unroll
       for (int t = 0; t < kDotChunk; ++t)
         if (t < cnt) {
-          const double2 v = to_d(Vb[(long long)(i0 + t) * ldv + e]);
-          acc[t].x += v.x * we.x + v.y * we.y;
-          acc[t].y += v.x * we.y - v.y * we.x;
+          const int i = i0 + t;
+          const TB v = (i < k) ? Vb[(long long)i * ldv + e] : we;
+          ar[t] += v.x * we.x + v.y * we.y;
+          ai[t] += v.x * we.y - v.y * we.x;
         }
     }
 #pragma unroll
     for (int t = 0; t < kDotChunk; ++t) {
-      double2 a = acc[t];
+      double2 a = make_double2((double)ar[t], (double)ai[t]);
       for (int off = 16; off > 0; off >>= 1) {
         a.x += __shfl_down_sync(0xffffffffu, a.x, off);
         a.y += __shfl_down_sync(0xffffffffu, a.y, off);
@@ -126,9 +143,9 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__
     }
     __syncthreads();
     if (threadIdx.x < cnt) {
-      double2 s = make_double2(0, 0);
-      for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) s = s + red[wgi][threadIdx.x];
-      partial[(long long)(i0 + threadIdx.x) * G + blockIdx.x] = s;
+      double2 sm = make_double2(0, 0);
+      for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) sm = sm + red[wgi][threadIdx.x];
+      partial[(long long)(i0 + threadIdx.x) * G + blockIdx.x] = sm;
     }
     __syncthreads();
   }
@@ -153,23 +170,65 @@ __global__ void k_reduce_partials(const double2* __restrict__ partial, int k, in
   }
 }
 
-// w -= sum_i coef[i] V_i  (coef on the device, FP64)
-template <typename TB, typename TW>
-__global__ void k_multiaxpy(TW* __restrict__ w, const TB* __restrict__ Vb, long long ldv, int k,
-                            const double2* __restrict__ coef, long long L, double sign) {
-  __shared__ double2 cs[256];
-  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) cs[i] = coef[i];
+// w -= sum_i coef[i] V_i (coef on the device); if norm_partial, also the
+// block partial sums of |w|^2 after the update (slot blockIdx.x).
+template <typename TB>
+__global__ void __launch_bounds__(kRedThreads) k_axpy_norm(TB* __restrict__ w, const TB* __restrict__ Vb, long long ldv,
+                                                           int k, const double2* __restrict__ coef, long long L,
+                                                           double2* norm_partial) {
+  typedef typename Acc<TB>::T AT;
+  __shared__ typename Acc<TB>::V cs[256];
+  __shared__ double red[kRedThreads / 32];
+  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) {
+    cs[i].x = (AT)coef[i].x;
+    cs[i].y = (AT)coef[i].y;
+  }
+  __syncthreads();
+  AT nn = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
+    TB acc = w[e];
+    for (int i = 0; i < k; ++i) {
+      const TB v = Vb[(long long)i * ldv + e];
+      const typename Acc<TB>::V c = cs[i];
+      acc.x -= c.x * v.x - c.y * v.y;
+      acc.y -= c.x * v.y + c.y * v.x;
+    }
+    w[e] = acc;
+    nn += acc.x * acc.x + acc.y * acc.y;
+  }
+  if (norm_partial) {
+    double d = (double)nn;
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int j = 0; j < kRedThreads / 32; ++j) t += red[j];
+      norm_partial[blockIdx.x] = make_double2(t, 0.0);
+    }
+  }
+}
+
+// x += sum_i coef[i] V_i with x FP64 and V of type TB (products in TB's precision).
+template <typename TB>
+__global__ void k_update(double2* __restrict__ x, const TB* __restrict__ Vb, long long ldv, int k,
+                         const double2* __restrict__ coef, long long L) {
+  typedef typename Acc<TB>::T AT;
+  __shared__ typename Acc<TB>::V cs[256];
+  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) {
+    cs[i].x = (AT)coef[i].x;
+    cs[i].y = (AT)coef[i].y;
+  }
   __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
-    double2 acc = to_d(w[e]);
+    AT ax = 0, ay = 0;
     for (int i = 0; i < k; ++i) {
-      const double2 v = to_d(Vb[(long long)i * ldv + e]);
-      const double2 c = cs[i];
-      acc.x += sign * (c.x * v.x - c.y * v.y);
-      acc.y += sign * (c.x * v.y + c.y * v.x);
+      const TB v = Vb[(long long)i * ldv + e];
+      ax += cs[i].x * v.x - cs[i].y * v.y;
+      ay += cs[i].x * v.y + cs[i].y * v.x;
     }
-    w[e].x = acc.x;
-    w[e].y = acc.y;
+    x[e].x += (double)ax;
+    x[e].y += (double)ay;
   }
 }
 
@@ -191,44 +250,54 @@ __global__ void k_bminus(double2* __restrict__ r, const double2* __restrict__ b,
 static int ew_blocks(long long L) { return (int)std::min<long long>((L + 255) / 256, 152LL * 8); }
 
 struct KrylovBufs {
-  double2* partial = nullptr;  // [(m+1) * G]
-  double2* hdev = nullptr;     // [m+2]
+  double2* partial = nullptr;  // [(m+2) * G]
+  double2* hdev = nullptr;     // [2 (m+3)]
   double2* r = nullptr;        // FP64 residual / work
   double2* w64 = nullptr;      // FP64 Arnoldi vector
   float2* w32 = nullptr;       // FP32 Arnoldi vector
   void* V = nullptr;           // basis (m+1) x L, FP64 or FP32
 };
 
-template <typename TB, typename TW>
-static vie_status multidot(const TB* V, long long L, int k, const TW* w, KrylovBufs& kb, std::vector<cd>& h,
-                           cudaStream_t st) {
-  k_multidot<TB, TW><<<kRedBlocks, kRedThreads, 0, st>>>(V, L, k, w, L, kb.partial);
-  VIE_CK(cudaGetLastError());
-  k_reduce_partials<<<k, 256, 0, st>>>(kb.partial, k, kRedBlocks, kb.hdev);
-  VIE_CK(cudaGetLastError());
-  h.resize(k);
-  VIE_CK(cudaMemcpyAsync(h.data(), kb.hdev, sizeof(double2) * k, cudaMemcpyDeviceToHost, st));
-  VIE_CK(cudaStreamSynchronize(st));
-  return VIE_OK;
-}
-
-template <typename TB, typename TW>
-static vie_status multiaxpy(TW* w, const TB* V, long long L, const std::vector<cd>& c, KrylovBufs& kb, double sign,
-                            cudaStream_t st) {
-  const int k = (int)c.size();
-  VIE_CK(cudaMemcpyAsync(kb.hdev, c.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, st));
-  k_multiaxpy<TB, TW><<<ew_blocks(L), 256, 0, st>>>(w, V, L, k, kb.hdev, L, sign);
-  VIE_CK(cudaGetLastError());
-  return VIE_OK;
-}
-
-static double nrm_of(const std::vector<cd>& v) { return std::sqrt(std::max(0.0, v[0].real())); }
-
-// One GMRES(m) cycle on the operator applied in precision TB (basis type TB).
-//   rhs r (FP64, norm beta), result d (FP64) += V y.  Returns the number of
-//   Arnoldi steps taken and the estimated residual |g_{j+1}|.
+// h[0..k-1] = V^H w (+ slot k = |w|^2 if with_self), left on the device in kb.hdev + off.
 template <typename TB>
-static vie_status gmres_cycle(vie_problem* P, const double2* r, double beta, double2* d, int m, double stop_abs,
+static vie_status dots_dev(const TB* V, long long L, int k, const TB* w, bool with_self, KrylovBufs& kb, int off,
+                           cudaStream_t st) {
+  const int kt = k + (with_self ? 1 : 0);
+  k_multidot<TB><<<kRedBlocks, kRedThreads, 0, st>>>(V, L, k, w, L, kb.partial, with_self ? 1 : 0);
+  VIE_CK(cudaGetLastError());
+  k_reduce_partials<<<kt, 256, 0, st>>>(kb.partial, kt, kRedBlocks, kb.hdev + off);
+  VIE_CK(cudaGetLastError());
+  return VIE_OK;
+}
+
+// w -= V h (h at kb.hdev + hoff on the device); |w|^2 to kb.hdev + noff.
+template <typename TB>
+static vie_status axpy_norm_dev(TB* w, const TB* V, long long L, int k, KrylovBufs& kb, int hoff, int noff,
+                                cudaStream_t st) {
+  k_axpy_norm<TB><<<kRedBlocks, kRedThreads, 0, st>>>(w, V, L, k, kb.hdev + hoff, L, kb.partial);
+  VIE_CK(cudaGetLastError());
+  k_reduce_partials<<<1, 256, 0, st>>>(kb.partial, 1, kRedBlocks, kb.hdev + noff);
+  VIE_CK(cudaGetLastError());
+  return VIE_OK;
+}
+
+static vie_status norm2(const double2* v, long long L, KrylovBufs& kb, double* out, cudaStream_t st) {
+  vie_status s = dots_dev<double2>(v, L, 1, v, false, kb, 0, st);
+  if (s != VIE_OK) return s;
+  double2 h;
+  VIE_CK(cudaMemcpyAsync(&h, kb.hdev, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  VIE_CK(cudaStreamSynchronize(st));
+  *out = std::sqrt(std::max(0.0, h.x));
+  return VIE_OK;
+}
+
+// One GMRES(m) cycle on the operator applied in the precision of TB (basis
+// type TB).  Arnoldi by classical Gram-Schmidt with one device-resident
+// reduction per step and a second pass only when the projection removed
+// more than 3/4 of the norm (Kahan-Parlett "twice is enough").
+//   rhs r (FP64, norm beta); result x (FP64) += V y.
+template <typename TB>
+static vie_status gmres_cycle(vie_problem* P, const double2* r, double beta, double2* x, int m, double stop_abs,
                               KrylovBufs& kb, int* steps, double* est, int* applies, cudaStream_t st) {
   const long long L = (long long)P->ncomp * P->n * P->n * P->n;
   TB* V = (TB*)kb.V;
@@ -239,25 +308,36 @@ static vie_status gmres_cycle(vie_problem* P, const double2* r, double beta, dou
   std::vector<cd> Hm((size_t)(m + 1) * m, cd(0, 0)), cs(m), sn(m), g(m + 1, cd(0, 0));
   g[0] = beta;
   int j = 0;
-  std::vector<cd> h, h2, nn;
+  std::vector<double2> hb(2 * (m + 3));
   *est = beta;
+  const int H2 = m + 3;  // offset of the second-pass coefficients in hdev
   for (; j < m; ++j) {
     vie_status s = run_apply(P, P->kapply, V + (long long)j * L, w, prec, 1, true, st);
     if (s != VIE_OK) return s;
     ++*applies;
-    s = multidot(V, L, j + 1, w, kb, h, st);
+    s = dots_dev<TB>(V, L, j + 1, w, true, kb, 0, st);  // h, |w|^2 at slot j+1
     if (s != VIE_OK) return s;
-    s = multiaxpy(w, V, L, h, kb, -1.0, st);
+    s = axpy_norm_dev<TB>(w, V, L, j + 1, kb, 0, j + 2, st);  // |w'|^2 at slot j+2
     if (s != VIE_OK) return s;
-    s = multidot(V, L, j + 1, w, kb, h2, st);
-    if (s != VIE_OK) return s;
-    s = multiaxpy(w, V, L, h2, kb, -1.0, st);
-    if (s != VIE_OK) return s;
-    for (int i = 0; i <= j; ++i) h[i] += h2[i];
-    s = multidot(w, L, 1, w, kb, nn, st);
-    if (s != VIE_OK) return s;
-    const double hn = nrm_of(nn);
-    if (!std::isfinite(hn)) {
+    VIE_CK(cudaMemcpyAsync(hb.data(), kb.hdev, sizeof(double2) * (j + 3), cudaMemcpyDeviceToHost, st));
+    VIE_CK(cudaStreamSynchronize(st));
+    std::vector<cd> h(j + 1);
+    for (int i = 0; i <= j; ++i) h[i] = cd(hb[i].x, hb[i].y);
+    const double w0 = hb[j + 1].x;
+    double wn2 = hb[j + 2].x;
+    if (wn2 < 0.0625 * w0) {
+      // second Gram-Schmidt pass
+      s = dots_dev<TB>(V, L, j + 1, w, false, kb, H2, st);
+      if (s != VIE_OK) return s;
+      s = axpy_norm_dev<TB>(w, V, L, j + 1, kb, H2, H2 + j + 1, st);
+      if (s != VIE_OK) return s;
+      VIE_CK(cudaMemcpyAsync(hb.data() + H2, kb.hdev + H2, sizeof(double2) * (j + 2), cudaMemcpyDeviceToHost, st));
+      VIE_CK(cudaStreamSynchronize(st));
+      for (int i = 0; i <= j; ++i) h[i] += cd(hb[H2 + i].x, hb[H2 + i].y);
+      wn2 = hb[H2 + j + 1].x;
+    }
+    const double hn = std::sqrt(std::max(0.0, wn2));
+    if (!std::isfinite(hn) || !std::isfinite(w0)) {
       set_error("non-finite value in the Arnoldi process");
       return VIE_ENAN;
     }
@@ -291,8 +371,10 @@ static vie_status gmres_cycle(vie_problem* P, const double2* r, double beta, dou
     for (int q = i + 1; q < j; ++q) acc -= Hm[(size_t)i * m + q] * y[q];
     y[i] = acc / Hm[(size_t)i * m + i];
   }
-  vie_status s = multiaxpy(d, V, L, y, kb, +1.0, st);
-  if (s != VIE_OK) return s;
+  VIE_CK(cudaMemcpyAsync(kb.hdev, y.data(), sizeof(double2) * j, cudaMemcpyHostToDevice, st));
+  k_update<TB><<<ew_blocks(L), 256, 0, st>>>(x, V, L, j, kb.hdev, L);
+  VIE_CK(cudaGetLastError());
+  VIE_CK(cudaStreamSynchronize(st));  // y is a host temporary
   *steps = j;
   return VIE_OK;
 }
@@ -300,7 +382,7 @@ static vie_status gmres_cycle(vie_problem* P, const double2* r, double beta, dou
 static vie_status ensure_krylov(vie_problem* P, int m, bool mixed, KrylovBufs& kb) {
   const long long L = (long long)P->ncomp * P->n * P->n * P->n;
   const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
-  const size_t need = sizeof(double2) * ((size_t)(m + 1) * kRedBlocks + (m + 2)) + sizeof(double2) * 2 * L +
+  const size_t need = sizeof(double2) * ((size_t)(m + 2) * kRedBlocks + 2 * (m + 3)) + sizeof(double2) * 2 * L +
                       sizeof(float2) * L + esz * (size_t)(m + 1) * L + 4096;
   if (P->ks.bytes < need) {
     if (P->ks.buf) {
@@ -321,8 +403,8 @@ static vie_status ensure_krylov(vie_problem* P, int m, bool mixed, KrylovBufs& k
     p += (bytes + 255) & ~(size_t)255;
     return (void*)q;
   };
-  kb.partial = (double2*)take(sizeof(double2) * (size_t)(m + 1) * kRedBlocks);
-  kb.hdev = (double2*)take(sizeof(double2) * (m + 2));
+  kb.partial = (double2*)take(sizeof(double2) * (size_t)(m + 2) * kRedBlocks);
+  kb.hdev = (double2*)take(sizeof(double2) * 2 * (m + 3));
   kb.r = (double2*)take(sizeof(double2) * L);
   kb.w64 = (double2*)take(sizeof(double2) * L);
   kb.w32 = (float2*)take(sizeof(float2) * L);
@@ -345,10 +427,11 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
   for (int rr = 0; rr < opt->nrhs; ++rr) {
     const double2* b = (const double2*)rhs + rr * L;
     double2* x = (double2*)Jv + rr * L;
-    std::vector<cd> nb2;
-    s = multidot(b, L, 1, b, kb, nb2, st);
+    double nb = 0.0, nx = 0.0;
+    s = norm2(b, L, kb, &nb, st);
     if (s != VIE_OK) return s;
-    const double nb = nrm_of(nb2);
+    s = norm2(x, L, kb, &nx, st);
+    if (s != VIE_OK) return s;
     if (!(nb > 0.0) || !std::isfinite(nb)) {
       if (nb == 0.0) {
         VIE_CK(cudaMemsetAsync(x, 0, sizeof(double2) * L, st));
@@ -362,16 +445,20 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
     int total_inner = 0;
     const int max_outer = mixed ? opt->max_outer : std::max(1, opt->max_outer);
     for (int outer = 0; outer <= max_outer; ++outer) {
-      // FP64 residual r = b - A x
-      s = run_apply(P, P->kapply, x, kb.r, VIE_FP64, 1, true, st);
-      if (s != VIE_OK) return s;
-      ++inf.applies_fp64;
-      k_bminus<<<ew_blocks(L), 256, 0, st>>>(kb.r, b, L);
-      VIE_CK(cudaGetLastError());
-      std::vector<cd> rn;
-      s = multidot(kb.r, L, 1, kb.r, kb, rn, st);
-      if (s != VIE_OK) return s;
-      const double beta = nrm_of(rn);
+      // FP64 residual r = b - A x (r = b for a zero initial guess)
+      double beta = 0.0;
+      if (outer == 0 && nx == 0.0) {
+        VIE_CK(cudaMemcpyAsync(kb.r, b, sizeof(double2) * L, cudaMemcpyDeviceToDevice, st));
+        beta = nb;
+      } else {
+        s = run_apply(P, P->kapply, x, kb.r, VIE_FP64, 1, true, st);
+        if (s != VIE_OK) return s;
+        ++inf.applies_fp64;
+        k_bminus<<<ew_blocks(L), 256, 0, st>>>(kb.r, b, L);
+        VIE_CK(cudaGetLastError());
+        s = norm2(kb.r, L, kb, &beta, st);
+        if (s != VIE_OK) return s;
+      }
       if (!std::isfinite(beta)) {
         set_error("non-finite residual");
         return VIE_ENAN;

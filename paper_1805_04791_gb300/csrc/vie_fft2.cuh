@@ -1,0 +1,185 @@
+// Register-resident two-step FFT of length M = R1 * R2 for lines that are
+// processed by T = R2 threads each (R1 is a multiple of R2).
+//
+//   forward  X[k1 + R1 k2] = sum_{n2} W_R2^{n2 k2} W_M^{n2 k1} sum_{n1} W_R1^{n1 k1} x[R2 n1 + n2]
+//   inverse  x[R2 n1 + n2] = sum_{k1} W_R1^{-n1 k1} W_M^{-n2 k1} sum_{k2} W_R2^{-n2 k2} X[k1 + R1 k2]
+//
+// Step 1 of the forward transform runs in thread n2 (an R1-point DFT on its
+// registers), the twiddled result goes through shared memory once, and step 2
+// runs R1/T R2-point DFTs per thread.  After the forward transform thread t
+// holds X[k1 + R1 k2] for k1 = t + T j (j < R1/T) and all k2 -- exactly the
+// layout the inverse transform starts from, so a pointwise multiply in k-space
+// (the kernel mixing of the convolution) needs no data movement.
+// Pruning for zero padding: the forward input may be limited to its first
+// half (n1 < R1/2) and the inverse output to its first half (n1 < R1/2).
+//
+// Shared-memory transpose layout per line: rows of R2 + 1 (forward) or R1 + 1
+// (inverse) elements and an odd line pitch, so that 16 consecutive lines or
+// 16 consecutive rows hit distinct banks for 8-byte and 16-byte elements.
+#pragma once
+
+#include "vie_fft.cuh"
+
+namespace vie {
+
+// cos(pi j / 16), j = 0..31
+__device__ __forceinline__ double cos_pi16(int j) {
+  const double c[32] = {1.0,
+                        0.98078528040323044913,
+                        0.92387953251128675613,
+                        0.83146961230254523708,
+                        0.70710678118654752440,
+                        0.55557023301960222474,
+                        0.38268343236508977173,
+                        0.19509032201612826785,
+                        0.0,
+                        -0.19509032201612826785,
+                        -0.38268343236508977173,
+                        -0.55557023301960222474,
+                        -0.70710678118654752440,
+                        -0.83146961230254523708,
+                        -0.92387953251128675613,
+                        -0.98078528040323044913,
+                        -1.0,
+                        -0.98078528040323044913,
+                        -0.92387953251128675613,
+                        -0.83146961230254523708,
+                        -0.70710678118654752440,
+                        -0.55557023301960222474,
+                        -0.38268343236508977173,
+                        -0.19509032201612826785,
+                        0.0,
+                        0.19509032201612826785,
+                        0.38268343236508977173,
+                        0.55557023301960222474,
+                        0.70710678118654752440,
+                        0.83146961230254523708,
+                        0.92387953251128675613,
+                        0.98078528040323044913};
+  return c[j & 31];
+}
+
+// a * W_R^{S j} with W_R = exp(2 pi i / R) (R divides 32)
+template <int R, int S, typename T>
+__device__ __forceinline__ typename CT<T>::V twc(typename CT<T>::V a, int j) {
+  const int q = (j * (32 / R)) & 31;  // angle pi q / 16
+  const T c = (T)cos_pi16(q);
+  const T s = (T)S * (T)cos_pi16(q + 24);  // sin(pi q/16) = cos(pi (q - 8)/16)
+  return CT<T>::make(c * a.x - s * a.y, c * a.y + s * a.x);
+}
+
+template <int S, typename T> struct Dft<32, S, T> {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    V e[16], o[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      e[r] = u[2 * r];
+      o[r] = u[2 * r + 1];
+    }
+    Dft<16, S, T>::run(e);
+    Dft<16, S, T>::run(o);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const V t = (q == 0) ? o[0] : twc<32, S, T>(o[q], q);
+      u[q] = e[q] + t;
+      u[q + 16] = e[q] - t;
+    }
+  }
+};
+
+// DFT_R of u[0..R/2-1] followed by R/2 zeros (decimation in frequency).
+template <int R, int S, typename T>
+__device__ __forceinline__ void dft_half_in(typename CT<T>::V* u) {
+  typedef typename CT<T>::V V;
+  constexpr int H = R / 2;
+  V a[H], b[H];
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    a[r] = u[r];
+    b[r] = (r == 0) ? u[0] : twc<R, S, T>(u[r], r);
+  }
+  Dft<H, S, T>::run(a);
+  Dft<H, S, T>::run(b);
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    u[2 * m] = a[m];
+    u[2 * m + 1] = b[m];
+  }
+}
+
+// First R/2 outputs of the DFT_R of u[0..R-1] (decimation in time).
+template <int R, int S, typename T>
+__device__ __forceinline__ void dft_half_out(typename CT<T>::V* u) {
+  typedef typename CT<T>::V V;
+  constexpr int H = R / 2;
+  V a[H], b[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    a[m] = u[2 * m];
+    b[m] = u[2 * m + 1];
+  }
+  Dft<H, S, T>::run(a);
+  Dft<H, S, T>::run(b);
+#pragma unroll
+  for (int n = 0; n < H; ++n) u[n] = a[n] + ((n == 0) ? b[0] : twc<R, S, T>(b[n], n));
+}
+
+template <typename T, int R1, int R2>
+struct Fft2 {
+  typedef typename CT<T>::V V;
+  static constexpr int M = R1 * R2;
+  static constexpr int NT = R2;          // threads per line
+  static constexpr int J = R1 / R2;      // k1 rows per thread
+  static constexpr int PF = R2 + 1;      // forward transpose row pitch
+  static constexpr int PI = R1 + 1;      // inverse transpose row pitch
+  static constexpr int LS0 = (R1 * PF > R2 * PI ? R1 * PF : R2 * PI);
+  static constexpr int LS = (LS0 % 2 == 0) ? LS0 + 1 : LS0;  // odd line pitch
+
+  // Step 1 forward.  u[n1] = x[R2 n1 + t]; HALF: only n1 < R1/2 are nonzero.
+  template <bool HALF>
+  static __device__ __forceinline__ void fwd1(V* u, int t, V* s, const V* tw) {
+    if (HALF) dft_half_in<R1, -1, T>(u);
+    else Dft<R1, -1, T>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      V v = u[k1];
+      if (k1 != 0) v = cmul(v, tw[t * k1]);
+      s[k1 * PF + t] = v;
+    }
+  }
+  // Step 2 forward: X[j][k2] = X[k1 = t + R2 j][k2].
+  static __device__ __forceinline__ void fwd2(V (*X)[R2], int t, const V* s) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k1 = t + R2 * j;
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) X[j][n2] = s[k1 * PF + n2];
+      Dft<R2, -1, T>::run(X[j]);
+    }
+  }
+  // Step A inverse from the forward layout.
+  static __device__ __forceinline__ void invA(V (*X)[R2], int t, V* s, const V* tw) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k1 = t + R2 * j;
+      Dft<R2, +1, T>::run(X[j]);
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) {
+        V v = X[j][n2];
+        if (n2 != 0 && k1 != 0) v = cmulc(v, tw[n2 * k1]);
+        s[n2 * PI + k1] = v;
+      }
+    }
+  }
+  // Step B inverse: u[n1] = x[R2 n1 + t]; HALF: only n1 < R1/2 are produced.
+  template <bool HALF>
+  static __device__ __forceinline__ void invB(V* u, int t, const V* s) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) u[k1] = s[t * PI + k1];
+    if (HALF) dft_half_out<R1, +1, T>(u);
+    else Dft<R1, +1, T>::run(u);
+  }
+};
+
+}  // namespace vie

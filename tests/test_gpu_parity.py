@@ -262,3 +262,75 @@ def test_full_size_helmholtz_128_fp32(vie):
     yo = op.apply(x.astype(np.complex64).astype(np.complex128))
     assert rel(y64.cpu().numpy(), yo) <= 1e-12
     assert rel(y32.cpu().numpy(), yo) <= 2e-5
+
+
+def gaussian_fields(n, alpha=36.0):
+    import vie_inputs as vi_
+
+    Z, Y, X = vi_.grid_coords(n, -1.0, 1.0)
+    psi = np.exp(-alpha * (X * X + Y * Y + Z * Z))
+    grad = np.stack([-2 * alpha * X * psi, -2 * alpha * Y * psi, -2 * alpha * Z * psi]).astype(np.complex128)
+    curl = np.stack([-2 * alpha * Y * psi, 2 * alpha * X * psi, 0 * psi]).astype(np.complex128)
+    return grad, curl
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_lemma2_eigenfields_at_full_size(vie, n, kind):
+    """Property that holds at any size (Lemma 2): with a constant isotropic eps = e I
+    (H = h I, h = (e-1)/(e+1)) the operator maps grad psi and curl P of a resolved
+    Gaussian to multiples of themselves:
+      Laplace   A grad psi = (1 + h) grad psi,  A curl P = (1 - h) curl P;
+      Helmholtz A curl P = (1 + h) curl P (for every w).
+    Checks every pass, the kernels and the H epilogue at the sizes the configurations use."""
+    import torch
+
+    e = 3.0
+    h = (e - 1) / (e + 1)
+    eps = np.zeros((9, n, n, n), np.complex128)
+    for a in range(3):
+        eps[4 * a] = e
+    omega = 0.0 if kind == "laplace" else 4 * math.pi
+    P = vie.Problem(kind, n, -1.0, 1.0, omega, to_dev(eps))
+    del eps
+    grad, curl = gaussian_fields(n)
+    cases = [(curl, (1 - h) if kind == "laplace" else (1 + h))]
+    if kind == "laplace":
+        cases.append((grad, 1 + h))
+    for field, lam in cases:
+        for prec, dt, tol in ((vie.VIE_FP64, torch.complex128, 1e-11), (vie.VIE_FP32, torch.complex64, 2e-5)):
+            xd = to_dev(field, dt)
+            yd = torch.empty_like(xd)
+            P.apply(xd, yd, prec)
+            torch.cuda.synchronize()
+            got = yd.to(torch.complex128)
+            ref = lam * xd.to(torch.complex128)
+            err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+            assert err <= tol, (kind, n, prec, err)
+    P.close()
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_fast_and_generic_paths_agree_with_oracle(vie, n, monkeypatch):
+    """Both the register-resident kernels (2n in {64,128,256,512}) and the generic
+    shared-memory Stockham kernels reproduce the oracle."""
+    import torch
+
+    p = vi.helmholtz_problem(n=n, wavelengths=3.0, seed=5)
+    op = operators.OracleProblem.from_problem(p)
+    x = vi.random_field(n, 3, 6)[0]
+    yo = op.apply(x)
+    outs = []
+    for generic in (False, True):
+        if generic:
+            monkeypatch.setenv("VIE_GENERIC_FFT", "1")
+        P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, eps_dev(p))
+        xd = to_dev(x)
+        yd = torch.empty_like(xd)
+        P.apply(xd, yd, vie.VIE_FP64)
+        torch.cuda.synchronize()
+        outs.append(yd.cpu().numpy())
+        P.close()
+    monkeypatch.delenv("VIE_GENERIC_FFT", raising=False)
+    for y in outs:
+        assert rel(y, yo) <= 1e-12
