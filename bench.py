@@ -33,6 +33,24 @@ sys.path.insert(0, ROOT)
 
 N_BUFS = 8  # rotating input/output buffers: 8 x 2 x 50 MB > 129 MB L2
 
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of the dominant kernel, with the hash of the kernel sources it was measured
+# on; reported only while the sources are unchanged (profiles/ has the capture).
+MEASURED_TRAFFIC = {"kernel": "P3_z_kernel_z", "n": 128, "sources_sha1_16": "051a9781eb7739cd",
+                    "bytes": 452.2e6}
+KERNEL_SOURCES = ["paper_1805_04791_gb300/csrc/apply.cu", "paper_1805_04791_gb300/csrc/vie_fft2.cuh",
+                  "paper_1805_04791_gb300/csrc/vie_fft.cuh"]
+
+
+def sources_sha():
+    import hashlib
+
+    parts = []
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            parts.append(hashlib.sha1(fh.read()).hexdigest())
+    return hashlib.sha1(("".join(p + "\n" for p in parts)).encode()).hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -44,6 +62,9 @@ def parse():
     ap.add_argument("--solves", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--case", default=None, choices=["apply"],
+                    help="minimal run for profilers: build the problem, run --reps FP32 applies, exit")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -377,7 +398,11 @@ def run_ours(args):
             "apply_alg_bytes": apply_bytes, "apply_alg_gbs": apply_bytes / (total_ms / args.steps / 1000.0) / 1e9,
             "kernels": kernels,
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": None},
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (MEASURED_TRAFFIC["bytes"] if (MEASURED_TRAFFIC["kernel"] == names[dom]
+                                     and MEASURED_TRAFFIC["n"] == n
+                                     and MEASURED_TRAFFIC["sources_sha1_16"] == sources_sha()) else None),
+                         "alg_bytes": abytes[dom]},
             "solve": solve, "setup_s": t_setup, "wall_s_timed": t_wall,
             "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk, "cpu_baseline": cpu,
         }
@@ -389,9 +414,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    dev = torch.device("cuda:0")
+    n = args.n
+    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
+    P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev))
+    x = torch.randn((3, n, n, n), dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(args.reps):
+        P.apply(x, y, vie.VIE_FP32)
+    torch.cuda.synchronize()
+    P.close()
+    print("case ok")
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.case == "apply":
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
