@@ -32,7 +32,12 @@
  * - No exception crosses the ABI; every call returns a vie_status and, on
  *   failure, vie_last_error() returns a message (thread-local).
  * - A problem handle is not thread-safe; distinct handles may be used from
- *   different threads on different streams.
+ *   different threads on different streams.  Calls on one handle must be
+ *   ordered (one stream, or streams the caller synchronises).  Device memory
+ *   is allocated stream-ordered (cudaMallocAsync) on the stream of the call,
+ *   so calls on other handles and streams are never serialised by it; the
+ *   stream given to vie_problem_create must stay valid until
+ *   vie_problem_destroy, which frees on it.
  */
 #ifndef VIE_H
 #define VIE_H
@@ -144,8 +149,19 @@ vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, in
  * admission by memory budget.  has_mu: 1 for Maxwell with mu. */
 size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu);
 
-/* Release every allocation of the handle (synchronises the device). */
+/* Release every allocation of the handle, stream-ordered on the stream the
+ * handle was created with, and wait for that stream. */
 vie_status vie_problem_destroy(vie_problem* P);
+
+/* Autotune the z-pass schedule (pencils per CTA, one CTA per mirror group of
+ * tiles or one per tile) of vie_apply at this precision by timing every
+ * applicable variant on this device; the choice is kept in the handle and
+ * written to *variant (-1: the shape uses the generic kernels).  vie_apply
+ * tunes on its first call for a precision anyway; calling vie_tune first keeps
+ * the tuning time out of a timed or captured region.  Synchronises the stream.
+ * Environment: VIE_TUNE=0 takes the first applicable variant without timing,
+ * VIE_P3_VARIANT=k forces variant k. */
+vie_status vie_tune(vie_problem* P, int precision, int* variant, void* stream);
 
 /* Per-kernel timing of vie_apply / vie_eval_scattered, for measurement tools.
  * vie_profile_begin(P, cap) makes the following applies on P record a CUDA

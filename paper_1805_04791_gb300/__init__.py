@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "VIE_OK", 1: "VIE_EINVAL", 2: "VIE_ENOMEM", 3: "VIE_ECUDA", 4
 
 EXPORTED = ("vie_problem_create", "vie_problem_ncomp", "vie_apply", "vie_rhs_plane_wave", "vie_solve",
             "vie_eval_scattered", "vie_problem_bytes", "vie_problem_destroy", "vie_last_error",
-            "vie_profile_begin", "vie_profile_end")
+            "vie_profile_begin", "vie_profile_end", "vie_tune")
 
 
 class VieError(RuntimeError):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.vie_profile_begin.restype = c_int
     lib.vie_profile_end.argtypes = [vp, ctypes.POINTER(c_double), c_int, ctypes.POINTER(c_int)]
     lib.vie_profile_end.restype = c_int
+    lib.vie_tune.argtypes = [vp, c_int, ctypes.POINTER(c_int), vp]
+    lib.vie_tune.restype = c_int
     lib.vie_last_error.argtypes = []
     lib.vie_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -169,6 +171,12 @@ def vie_profile_end(P, nslots: int = 5):
     return list(ms), cnt.value
 
 
+def vie_tune(P, precision: int, stream=None) -> int:
+    v = ctypes.c_int()
+    _check(load().vie_tune(P, precision, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
 def vie_last_error() -> str:
     return load().vie_last_error().decode()
 
@@ -199,6 +207,9 @@ class Problem:
 
     def eval_scattered(self, J, out, nrhs=1, stream=None):
         vie_eval_scattered(self.handle, J, out, nrhs, stream)
+
+    def tune(self, precision=VIE_FP32, stream=None) -> int:
+        return vie_tune(self.handle, precision, stream)
 
     def close(self):
         if self.handle is not None:

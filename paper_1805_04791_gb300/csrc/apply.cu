@@ -18,6 +18,8 @@
 // inverse DFT folded in.
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "vie_fft2.cuh"
 #include "vie_internal.h"
@@ -344,115 +346,6 @@ __global__ void __launch_bounds__(256) f_py(const typename CT<T>::V* __restrict_
   }
 }
 
-// z-pencils of the three components: forward, kernel mixing (KM_SYM3 or
-// KM_DIV), inverse, keep z < n.  CTA order pairs the mirror pencils
-// (ky, M - ky) x (kx tile, mirrored kx tile) so that the four CTAs reading the
-// same kernel octant entries run together and share them through L2.
-// SLAB: the kernel values of the tile (narr arrays x (n+1) octant z values x L
-// pencils) are staged in shared memory by coalesced loads issued together with
-// the pencil loads, so the mixing reads no global memory.
-template <typename T, int R1, int R2, bool SLAB>
-__global__ void __launch_bounds__(256) f_p3(typename CT<T>::V* __restrict__ B, int n, int C,
-                                            const typename CT<T>::V* __restrict__ K, int mode,
-                                            const typename CT<T>::V* __restrict__ twg) {
-  typedef Fft2<T, R1, R2> F;
-  typedef typename CT<T>::V V;
-  constexpr int M = F::M, L = 256 / R2, NTX = M / L;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  V* tw = (V*)smraw;
-  V* sm = tw + M;
-  V* ks = sm + L * F::LS;  // [narr][n+1][L]
-  // block -> (ky, kx tile)
-  const int v = blockIdx.x & 3, g = blockIdx.x >> 2;
-  const int kyp = g / (NTX / 2), txp = g - kyp * (NTX / 2);
-  if ((v & 1) && (kyp == 0 || kyp == M / 2)) return;  // self-mirrored rows
-  const int ky = (v & 1) ? M - kyp : kyp;
-  const int tile = (v & 2) ? NTX - 1 - txp : txp;
-  load_tw(tw, twg, M);
-  const int l = threadIdx.x % L, t = threadIdx.x / L;
-  const int kx = tile * L + l;
-  const int b = blockIdx.y;
-  const long long zs = (long long)M * M, cs = (long long)n * zs;
-  V* base = B + (long long)b * C * cs + (long long)ky * M + kx;
-  V* s = sm + l * F::LS;
-  const int cout = (mode == KM_DIV) ? 1 : 3;
-  const int narr = (mode == KM_DIV) ? 3 : 6;
-  const int O = n + 1;
-  const long long O3 = (long long)O * O * O;
-  V X[3][F::J][R2];
-  // issue the loads of all three components before any compute
-  V u3[3][R1 / 2];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int n1 = 0; n1 < R1 / 2; ++n1) u3[c][n1] = base[c * cs + (long long)(R2 * n1 + t) * zs];
-  if (SLAB) {
-    const int oy = ky <= n ? ky : M - ky;
-    const int tot = narr * O * L;
-    for (int idx = threadIdx.x; idx < tot; idx += 256) {
-      const int ll = idx % L, r = idx / L;
-      const int oz = r % O, a = r / O;
-      const int kxx = tile * L + ll;
-      const int ox = kxx <= n ? kxx : M - kxx;
-      ks[idx] = K[a * O3 + ((long long)oz * O + oy) * O + ox];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    V u[R1];
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) u[n1] = (n1 < R1 / 2) ? u3[c][n1] : CT<T>::make(0, 0);
-    F::template fwd1<true>(u, t, s, tw);
-    __syncthreads();
-    F::fwd2(X[c], t, s);
-    __syncthreads();
-  }
-  // kernel mixing at kz = t + R2 j + R1 k2
-  const int n_ = n;
-  const bool fy = ky > n, fx = kx > n;
-#pragma unroll
-  for (int j = 0; j < F::J; ++j)
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) {
-      const int kz = t + R2 * j + R1 * k2;
-      const V u0 = X[0][j][k2], u1 = X[1][j][k2], u2 = X[2][j][k2];
-      V q[6];
-      if (SLAB) {
-        const bool fz = kz > n;
-        const int oz = fz ? M - kz : kz;
-        for (int a = 0; a < narr; ++a) {
-          const int par = sym_parity(mode == KM_DIV ? 6 + a : a);
-          V vv = ks[(a * O + oz) * L + l];
-          const bool neg = ((par & 4) && fz) ^ ((par & 2) && fy) ^ ((par & 1) && fx);
-          if (neg) { vv.x = -vv.x; vv.y = -vv.y; }
-          q[a] = vv;
-        }
-      } else {
-        for (int a = 0; a < narr; ++a)
-          q[a] = kval(K, a, O3, O, sym_parity(mode == KM_DIV ? 6 + a : a), kz, ky, kx, n_);
-      }
-      if (mode == KM_DIV) {
-        X[0][j][k2] = cmul(q[0], u0) + cmul(q[1], u1) + cmul(q[2], u2);
-      } else {
-        X[0][j][k2] = cmul(q[0], u0) + cmul(q[3], u1) + cmul(q[4], u2);
-        X[1][j][k2] = cmul(q[3], u0) + cmul(q[1], u1) + cmul(q[5], u2);
-        X[2][j][k2] = cmul(q[4], u0) + cmul(q[5], u1) + cmul(q[2], u2);
-      }
-    }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (c >= cout) break;
-    F::invA(X[c], t, s, tw);
-    __syncthreads();
-    V u[R1];
-    F::template invB<true>(u, t, s);
-#pragma unroll
-    for (int n1 = 0; n1 < R1 / 2; ++n1) base[c * cs + (long long)(R2 * n1 + t) * zs] = u[n1];
-    __syncthreads();
-  }
-}
-
 // z-pencils, one component per thread group: CTA = NP pencils (consecutive
 // kx) x CMAX components x R2 threads.  Each group transforms its component
 // of its pencil (pruned forward FFT), parks the spectrum in shared memory,
@@ -599,8 +492,15 @@ f_p3b(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
 // mixing reads only shared memory.  The line pitch of the transpose buffers
 // is chosen so that 8 pencils x 2 threads (FP32) or 8 pencils (FP64) hit
 // distinct banks.
+template <int MODE, int NP, int R2>
+struct P3cThreads {
+  static constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
+  static constexpr int N = NP * R2 * CMAX;
+  static constexpr int MINB = N <= 384 ? 2 : 1;
+};
+
 template <typename T, int R1, int R2, int MODE, int NP>
-__global__ void __launch_bounds__(NP * R2 * (ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO), 2)
+__global__ void __launch_bounds__(P3cThreads<MODE, NP, R2>::N, P3cThreads<MODE, NP, R2>::MINB)
 f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* __restrict__ K,
       const typename CT<T>::V* __restrict__ twg) {
   typedef Fft2<T, R1, R2> F;
@@ -665,15 +565,17 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
     if (c < CO) {
       const bool fy = ky > n, fx = kx > n;
       const int q = (fx ? M - kx : kx) - NP * txp;
-      bool neg0[NT], zodd[NT];
+      // per term: kernel pointer, input spectrum, and the sign for kz <= n / kz > n
+      T sg0[NT], sg1[NT];
       const V* kp[NT];
       const V* xs[NT];
 #pragma unroll
       for (int i = 0; i < NT; ++i) {
         if (i >= ntm) break;
         const int par = sym_parity(MODE == KM_DIV ? 6 + ta[i] : ta[i]);
-        neg0[i] = (((par & 2) && fy) != ((par & 1) && fx)) != (tsg[i] < 0);
-        zodd[i] = (par & 4) != 0;
+        const bool neg0 = (((par & 2) && fy) != ((par & 1) && fx)) != (tsg[i] < 0);
+        sg0[i] = neg0 ? (T)-1 : (T)1;
+        sg1[i] = (neg0 != ((par & 4) != 0)) ? (T)-1 : (T)1;
         kp[i] = slab + ta[i] * O * QW + q;
         xs[i] = sm + (tb[i] * NP + l) * LS;
       }
@@ -682,17 +584,22 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
           const int k = t + R2 * j + R1 * k2;
-          const bool fz = k > n;
+          // k < n for k2 < R2/2 and k > n for k2 > R2/2 (k = R1 k2 + [0, R1)); only k2 = R2/2 depends on t, j
+          const bool fz = (k2 < R2 / 2) ? false : ((k2 > R2 / 2) ? true : (k > n));
           const int zoff = (fz ? M - k : k) * QW;
-          V acc = CT<T>::make(0, 0);
+          T ax = 0, ay = 0;
 #pragma unroll
           for (int i = 0; i < NT; ++i) {
             if (i >= ntm) break;
-            V kv = kp[i][zoff];
-            if (neg0[i] != (zodd[i] && fz)) { kv.x = -kv.x; kv.y = -kv.y; }
-            acc = acc + cmul(kv, xs[i][k]);
+            const V kv = kp[i][zoff];
+            const V xv = xs[i][k];
+            const T sgn = fz ? sg1[i] : sg0[i];
+            const T px = kv.x * xv.x - kv.y * xv.y;
+            const T py = kv.x * xv.y + kv.y * xv.x;
+            ax = fma(sgn, px, ax);
+            ay = fma(sgn, py, ay);
           }
-          X[j][k2] = acc;
+          X[j][k2] = CT<T>::make(ax, ay);
         }
     }
     __syncthreads();
@@ -706,12 +613,14 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
   }
 }
 
-// x-lines of all components: inverse, keep x < n, epilogue y = x + H u (or y = u).
-template <typename T, int R1, int R2>
+// x-lines of all components: inverse, keep x < n, epilogue y = x + H u (or
+// y = u).  CO = 3 (one H block) or 6 ([J; M] with H_eps and H_mu, or [E; H]).
+template <typename T, int R1, int R2, int CO>
 __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict__ A,
                                             const typename CT<T>::V* __restrict__ xin, typename CT<T>::V* __restrict__ y,
                                             int n, int C, int cout, const typename CT<T>::V* __restrict__ He,
-                                            int with_identity, const typename CT<T>::V* __restrict__ twg) {
+                                            const typename CT<T>::V* __restrict__ Hm, int with_identity,
+                                            const typename CT<T>::V* __restrict__ twg) {
   typedef Fft2<T, R1, R2> F;
   typedef typename CT<T>::V V;
   constexpr int M = F::M, L = 256 / R2, H2 = R1 / 2;
@@ -727,10 +636,10 @@ __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict_
   const long long N = (long long)rows * n;
   const long long cs = (long long)rows * M;
   V* s = sm + l * F::LS;
-  V uo[3][H2];
+  V uo[CO][H2];
   __syncthreads();
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < CO; ++c) {
     if (c >= cout) break;
     const V* src = A + ((long long)b * C + c) * cs + (long long)row * M;
     V X[F::J][R2];
@@ -751,17 +660,21 @@ __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict_
   for (int n1 = 0; n1 < H2; ++n1) {
     const long long pt = (long long)row * n + R2 * n1 + t;
     if (with_identity) {
-      const V hxx = He[pt], hyy = He[N + pt], hzz = He[2 * N + pt];
-      const V hxy = He[3 * N + pt], hxz = He[4 * N + pt], hyz = He[5 * N + pt];
-      const V* xi = xin + (long long)b * 3 * N + pt;
-      V* yo = y + (long long)b * 3 * N + pt;
-      const V a0 = uo[0][n1], a1 = uo[1][n1], a2 = uo[2][n1];
-      yo[0] = xi[0] + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2);
-      yo[N] = xi[N] + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2);
-      yo[2 * N] = xi[2 * N] + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2);
+#pragma unroll
+      for (int blk = 0; blk < CO / 3; ++blk) {
+        const V* H = blk == 0 ? He : Hm;
+        const V hxx = H[pt], hyy = H[N + pt], hzz = H[2 * N + pt];
+        const V hxy = H[3 * N + pt], hxz = H[4 * N + pt], hyz = H[5 * N + pt];
+        const V* xi = xin + ((long long)b * CO + 3 * blk) * N + pt;
+        V* yo = y + ((long long)b * CO + 3 * blk) * N + pt;
+        const V a0 = uo[3 * blk][n1], a1 = uo[3 * blk + 1][n1], a2 = uo[3 * blk + 2][n1];
+        yo[0] = xi[0] + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2);
+        yo[N] = xi[N] + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2);
+        yo[2 * N] = xi[2 * N] + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2);
+      }
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < CO; ++c)
         if (c < cout) y[((long long)b * cout + c) * N + pt] = uo[c][n1];
     }
   }
@@ -822,56 +735,64 @@ struct FastPath {
     constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
     constexpr int LS = (sizeof(V) == 8) ? ((F::LS0 + 13) / 16) * 16 + 2 : (F::LS0 | 1);
     constexpr int NTX = M / NP;
+    constexpr int NTHR = P3cThreads<MODE, NP, R2>::N;
     const size_t sm = sizeof(V) * (M + (size_t)CMAX * NP * LS + (size_t)NARR * (n + 1) * (NP + 1));
+    const size_t cap = P3cThreads<MODE, NP, R2>::MINB == 2 ? 112 * 1024 : 224 * 1024;
     *done = false;
-    if (sm > 112 * 1024 || NTX < 2) return VIE_OK;  // two CTAs per SM or not at all
-    VIE_CK(cudaFuncSetAttribute(f_p3c<T, R1, R2, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    f_p3c<T, R1, R2, MODE, NP><<<dim3((M / 2 + 1) * (NTX / 2), nrhs), NP * R2 * CMAX, sm, st>>>(B, n, C, K, tw);
-    VIE_CK(cudaGetLastError());
-    *done = true;
-    return VIE_OK;
-  }
-  static vie_status p3(V* B, int n, int C, const V* K, int mode, int nrhs, const V* tw, cudaStream_t st) {
-    if (!getenv("VIE_P3_B")) {
-      bool done = false;
-      vie_status e = VIE_OK;
-      switch (mode) {
-        case KM_SYM3: e = p3c<KM_SYM3, 8>(B, n, C, K, nrhs, tw, &done, st); break;
-        case KM_DIV: e = p3c<KM_DIV, 8>(B, n, C, K, nrhs, tw, &done, st); break;
-        case KM_EMRED: e = p3c<KM_EMRED, 4>(B, n, C, K, nrhs, tw, &done, st); break;
-        default: e = p3c<KM_MAXWELL6, 4>(B, n, C, K, nrhs, tw, &done, st); break;
-      }
-      if (e != VIE_OK || done) return e;
-    }
-    if (!getenv("VIE_P3_REG")) {
-      constexpr int NPS = (M / 8 >= 2) ? 8 : 4;
-      switch (mode) {
-        case KM_SYM3: return p3b<KM_SYM3, NPS>(B, n, C, K, nrhs, tw, st);
-        case KM_DIV: return p3b<KM_DIV, NPS>(B, n, C, K, nrhs, tw, st);
-        case KM_EMRED: return p3b<KM_EMRED, 4>(B, n, C, K, nrhs, tw, st);
-        default: return p3b<KM_MAXWELL6, 4>(B, n, C, K, nrhs, tw, st);
-      }
-    }
-    constexpr int NTX = M / L;
-    const size_t slab = sizeof(V) * 6 * (size_t)(n + 1) * L;
-    const dim3 grid((M / 2 + 1) * (NTX / 2) * 4, nrhs);
-    if (smem() + slab <= 160 * 1024 && !getenv("VIE_NO_KSLAB")) {
-      const size_t sm = smem() + slab;
-      VIE_CK(cudaFuncSetAttribute(f_p3<T, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      f_p3<T, R1, R2, true><<<grid, 256, sm, st>>>(B, n, C, K, mode, tw);
+    if constexpr (NTHR > 1024 || NTX < 2) {
+      return VIE_OK;  // shape not expressible: not instantiated
     } else {
-      VIE_CK(cudaFuncSetAttribute(f_p3<T, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem()));
-      f_p3<T, R1, R2, false><<<grid, 256, smem(), st>>>(B, n, C, K, mode, tw);
+      if (sm > cap) return VIE_OK;
+      VIE_CK(cudaFuncSetAttribute(f_p3c<T, R1, R2, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      f_p3c<T, R1, R2, MODE, NP><<<dim3((M / 2 + 1) * (NTX / 2), nrhs), NTHR, sm, st>>>(B, n, C, K, tw);
+      VIE_CK(cudaGetLastError());
+      *done = true;
+      return VIE_OK;
     }
-    VIE_CK(cudaGetLastError());
-    return VIE_OK;
   }
-  static vie_status p5(const V* A, const V* xin, V* y, int n, int C, int cout, const V* He, bool wid, int nrhs,
-                       const V* tw, cudaStream_t st) {
-    VIE_CK(cudaFuncSetAttribute(f_p5<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
-    f_p5<T, R1, R2><<<dim3((n * n + L - 1) / L, nrhs), 256, smem(), st>>>(A, xin, y, n, C, cout, He, wid ? 1 : 0,
-                                                                           tw);
+  template <int MODE, int NP>
+  static vie_status p3b_ok(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
+    constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
+    *done = false;
+    if constexpr (NP * R2 * CMAX > 1024 || M / NP < 2) {
+      return VIE_OK;
+    } else {
+      vie_status e = p3b<MODE, NP>(B, n, C, K, nrhs, tw, st);
+      *done = (e == VIE_OK);
+      return e;
+    }
+  }
+  template <int MODE>
+  static vie_status p3_mode(int variant, V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done,
+                            cudaStream_t st) {
+    switch (variant) {
+      case 0: return p3c<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
+      case 1: return p3c<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
+      case 2: return p3c<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
+      case 3: return p3b_ok<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
+      default: return p3b_ok<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
+    }
+  }
+  // Run P3 variant `variant` (0..kP3Variants-1); *done = false if it does not apply to this shape.
+  static vie_status p3v(int variant, V* B, int n, int C, const V* K, int mode, int nrhs, const V* tw, bool* done,
+                        cudaStream_t st) {
+    switch (mode) {
+      case KM_SYM3: return p3_mode<KM_SYM3>(variant, B, n, C, K, nrhs, tw, done, st);
+      case KM_DIV: return p3_mode<KM_DIV>(variant, B, n, C, K, nrhs, tw, done, st);
+      case KM_EMRED: return p3_mode<KM_EMRED>(variant, B, n, C, K, nrhs, tw, done, st);
+      default: return p3_mode<KM_MAXWELL6>(variant, B, n, C, K, nrhs, tw, done, st);
+    }
+  }
+  static vie_status p5(const V* A, const V* xin, V* y, int n, int C, int cout, const V* He, const V* Hm, bool wid,
+                       int nrhs, const V* tw, cudaStream_t st) {
+    const dim3 grid((n * n + L - 1) / L, nrhs);
+    if (cout <= 3) {
+      VIE_CK(cudaFuncSetAttribute(f_p5<T, R1, R2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
+      f_p5<T, R1, R2, 3><<<grid, 256, smem(), st>>>(A, xin, y, n, C, cout, He, Hm, wid ? 1 : 0, tw);
+    } else {
+      VIE_CK(cudaFuncSetAttribute(f_p5<T, R1, R2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
+      f_p5<T, R1, R2, 6><<<grid, 256, smem(), st>>>(A, xin, y, n, C, cout, He, Hm, wid ? 1 : 0, tw);
+    }
     VIE_CK(cudaGetLastError());
     return VIE_OK;
   }
@@ -890,7 +811,7 @@ static FastSel fast_select(int M, int mode, bool with_identity) {
   f.p1 = true;
   f.py = true;
   f.p3 = true;
-  f.p5 = cout <= 3 && (!with_identity || cout == 3) && cin <= 3;
+  f.p5 = (cout <= 3 || cout == 6) && (!with_identity || cout == cin);
   return f;
 }
 
@@ -905,11 +826,20 @@ static vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const 
   switch (pass) {
     case 1: return FP::p1((const V*)in, A, n, C, cin, nrhs, tw, st);
     case 2: return FP::template py<-1>(A, B, n, C, cin, nrhs, tw, st);
-    case 3: return FP::p3(B, n, C, Prec<T>::K(K), K.mode, nrhs, tw, st);
+    case 3: {
+      bool done = false;
+      vie_status e = FP::p3v(P->p3_variant[sizeof(T) == 8 ? 0 : 1][K.mode], B, n, C, Prec<T>::K(K), K.mode, nrhs,
+                             tw, &done, st);
+      if (e == VIE_OK && !done) {
+        set_error("selected z-pass variant does not apply to this shape");
+        return VIE_EINVAL;
+      }
+      return e;
+    }
     case 4: return FP::template py<+1>(B, A, n, C, cout, nrhs, tw, st);
     default:
-      return FP::p5(A, (const V*)in, (V*)out, n, C, cout, Prec<T>::H(P->He64, P->He32), with_identity, nrhs, tw,
-                    st);
+      return FP::p5(A, (const V*)in, (V*)out, n, C, cout, Prec<T>::H(P->He64, P->He32),
+                    P->has_mu ? Prec<T>::H(P->Hm64, P->Hm32) : nullptr, with_identity, nrhs, tw, st);
   }
 }
 
@@ -925,6 +855,77 @@ static vie_status fast_dispatch(int pass, vie_problem* P, const KernelSet& K, co
   }
 }
 
+// Autotuner for the z pass: every applicable variant (mirror-group CTAs with
+// 8, 16 or 4 pencils, or one tile per CTA with 8 or 4 pencils) is launched once
+// to warm up and then timed over 3 launches with CUDA events on the buffer B
+// (whose contents are scratch at this point); the fastest is kept for the
+// problem's (precision, mode).  VIE_TUNE=0 takes the first applicable variant;
+// VIE_P3_VARIANT=k forces variant k.
+static const int kP3Variants = 5;
+
+static std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+static std::map<long long, int>& tune_cache() {
+  static std::map<long long, int> c;
+  return c;
+}
+
+template <typename T, int R1, int R2>
+static vie_status tune_p3(vie_problem* P, const KernelSet& K, typename CT<T>::V* B, int C, cudaStream_t st,
+                          int* best) {
+  typedef FastPath<T, R1, R2> FP;
+  const typename CT<T>::V* tw = Prec<T>::tw(P);
+  const char* force = getenv("VIE_P3_VARIANT");
+  const char* tune = getenv("VIE_TUNE");
+  const bool timed = !(tune && tune[0] == '0');
+  *best = -1;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  VIE_CK(cudaEventCreate(&e0));
+  VIE_CK(cudaEventCreate(&e1));
+  for (int v = 0; v < kP3Variants; ++v) {
+    if (force && atoi(force) != v) continue;
+    bool done = false;
+    vie_status s = FP::p3v(v, B, P->n, C, Prec<T>::K(K), K.mode, 1, tw, &done, st);
+    if (s != VIE_OK) return s;
+    if (!done) continue;
+    if (!timed || force) {
+      *best = v;
+      break;
+    }
+    VIE_CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) FP::p3v(v, B, P->n, C, Prec<T>::K(K), K.mode, 1, tw, &done, st);
+    VIE_CK(cudaEventRecord(e1, st));
+    VIE_CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    VIE_CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (*best < 0) {
+    set_error("no z-pass variant applies to this shape");
+    return VIE_EINVAL;
+  }
+  return VIE_OK;
+}
+
+template <typename T>
+static vie_status tune_dispatch(vie_problem* P, const KernelSet& K, typename CT<T>::V* B, int C, cudaStream_t st,
+                                int* best) {
+  switch (2 * P->n) {
+    case 64: return tune_p3<T, 8, 8>(P, K, B, C, st, best);
+    case 128: return tune_p3<T, 16, 8>(P, K, B, C, st, best);
+    case 256: return tune_p3<T, 16, 16>(P, K, B, C, st, best);
+    default: return tune_p3<T, 32, 16>(P, K, B, C, st, best);
+  }
+}
+
 template <typename T>
 static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
                               bool with_identity, cudaStream_t st) {
@@ -934,14 +935,12 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   const int C = std::max(cin, cout);
   const size_t need = apply_workspace_bytes(n, C, nrhs, sizeof(T) == 8 ? VIE_FP64 : VIE_FP32);
   if (P->ws.bytes < need) {
-    if (P->ws.buf) {
-      VIE_CK(cudaStreamSynchronize(st));
-      cudaFree(P->ws.buf);
-      P->ws.buf = nullptr;
-      P->ws.bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&P->ws.buf, need);
+    dfree(P->ws.buf, st);  // stream-ordered: earlier work on st completes first
+    P->ws.buf = nullptr;
+    P->ws.bytes = 0;
+    cudaError_t e = dalloc(&P->ws.buf, need, st);
     if (e != cudaSuccess) {
+      cudaGetLastError();
       set_error("out of device memory for the apply workspace");
       return VIE_ENOMEM;
     }
@@ -963,6 +962,24 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   }
 
   const FastSel fs = fast_select(M, K.mode, with_identity);
+  int& p3v = P->p3_variant[sizeof(T) == 8 ? 0 : 1][K.mode];
+  if (fs.p3 && p3v < 0) {
+    // one decision per (n, precision, mode) per process: every problem of a
+    // shape then runs the same arithmetic (bitwise-reproducible results)
+    const long long key = ((long long)P->n * 2 + (sizeof(T) == 8 ? 0 : 1)) * 8 + K.mode;
+    {
+      std::lock_guard<std::mutex> g(tune_mutex());
+      auto it = tune_cache().find(key);
+      if (it != tune_cache().end()) p3v = it->second;
+    }
+    if (p3v < 0) {
+      vie_status e = tune_dispatch<T>(P, K, B, C, st, &p3v);
+      if (e != VIE_OK) return e;
+      std::lock_guard<std::mutex> g(tune_mutex());
+      tune_cache().emplace(key, p3v);
+      p3v = tune_cache()[key];
+    }
+  }
   // P1
   if (fs.p1) {
     vie_status e = fast_dispatch<T>(1, P, K, in, out, nrhs, with_identity, A, B, C, st);
@@ -1037,6 +1054,33 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     if (rec) VIE_CK(cudaEventRecord(ev[5], st));
   }
   return VIE_OK;
+}
+
+vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant, cudaStream_t st) {
+  const int M = 2 * P->n;
+  if (!fast_select(M, K.mode, true).p3) {
+    *variant = -1;
+    return VIE_OK;
+  }
+  int& v = P->p3_variant[prec == VIE_FP64 ? 0 : 1][K.mode];
+  v = -1;
+  {
+    std::lock_guard<std::mutex> g(tune_mutex());
+    tune_cache().erase(((long long)P->n * 2 + (prec == VIE_FP64 ? 0 : 1)) * 8 + K.mode);
+  }
+  // an apply of a zero vector allocates the workspace and tunes on its first call
+  const long long L = (long long)cin_of(K.mode) * P->n * P->n * P->n;
+  void *x = nullptr, *y = nullptr;
+  const size_t esz = prec == VIE_FP64 ? sizeof(double2) : sizeof(float2);
+  VIE_CK(dalloc(&x, esz * L, st));
+  VIE_CK(dalloc(&y, esz * (size_t)cout_of(K.mode) * P->n * P->n * P->n, st));
+  VIE_CK(cudaMemsetAsync(x, 0, esz * L, st));
+  vie_status s = run_apply(P, K, x, y, prec, 1, K.mode == KM_SYM3 || K.mode == KM_MAXWELL6, st);
+  dfree(x, st);
+  dfree(y, st);
+  cudaStreamSynchronize(st);
+  *variant = v;
+  return s;
 }
 
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,

@@ -12,6 +12,16 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+cudaError_t dalloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+void dfree(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
 vie_status cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_ECUDA;
@@ -24,21 +34,21 @@ static bool smooth_size(int n) {
   return n == 1;
 }
 
-static void free_set(KernelSet& k) {
-  if (k.oct64) cudaFree(k.oct64);
-  if (k.oct32) cudaFree(k.oct32);
+static void free_set(KernelSet& k, cudaStream_t st) {
+  dfree(k.oct64, st);
+  dfree(k.oct32, st);
   k.oct64 = nullptr;
   k.oct32 = nullptr;
 }
 
 static void free_problem(vie_problem* P) {
   if (!P) return;
-  cudaDeviceSynchronize();
+  cudaStream_t st = P->stream;
   void* ptrs[] = {P->tw64, P->tw32, P->He64, P->He32, P->Hm64, P->Hm32, P->sym_oct, P->ws.buf, P->ks.buf, P->dflag};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
-  free_set(P->kapply);
-  free_set(P->keval);
+  for (void* q : ptrs) dfree(q, st);
+  free_set(P->kapply, st);
+  free_set(P->keval, st);
+  cudaStreamSynchronize(st);
   for (cudaEvent_t e : P->prof.ev) cudaEventDestroy(e);
   delete P;
 }
@@ -96,13 +106,14 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
   P->L = std::sqrt(3.0) * P->D;
   P->omega = kind == VIE_LAPLACE ? 0.0 : omega;
   cudaGetDevice(&P->device);
+  P->stream = st;
   if (!make_plan(2 * n, &P->plan2n)) {
     delete P;
     set_error("bad FFT size");
     return VIE_EINVAL;
   }
   vie_status s = VIE_OK;
-  cudaError_t e = cudaMalloc(&P->dflag, sizeof(int) * 4);
+  cudaError_t e = dalloc((void**)&P->dflag, sizeof(int) * 4, st);
   if (e != cudaSuccess) s = cuda_fail(e, "cudaMalloc(flag)");
   if (s == VIE_OK) s = make_twiddles(2 * n, &P->tw64, &P->tw32, st);
   if (s == VIE_OK) s = build_medium(P, eps, mu, st);
@@ -163,16 +174,28 @@ vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, in
 }
 
 size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu) {
+  if (n < 1 || nrhs < 1 || restart < 1) return 0;
   const size_t N = (size_t)n * n * n;
   const size_t O3 = (size_t)(n + 1) * (n + 1) * (n + 1);
   const int c = (kind == VIE_MAXWELL && has_mu) ? 6 : 3;
   const int nsym = kind == VIE_MAXWELL ? 10 : 9;
-  size_t b = 144 * N * (has_mu ? 2 : 1);                        // H: 6 entries, FP64 + FP32
-  b += 16 * O3 * nsym;                                          // raw symbol octants
-  b += 24 * O3 * 18;                                            // apply + eval sets, FP64 + FP32
-  b += apply_workspace_bytes(n, c, nrhs, VIE_FP64);             // padded intermediates
-  b += (size_t)nrhs * c * N * (8 * (restart + 1) + 16 * 2 + 8);  // mixed-precision Krylov
-  return b;
+  size_t held = 144 * N * (has_mu ? 2 : 1);  // H: 6 entries, FP64 + FP32
+  held += 16 * O3 * nsym;                    // raw symbol octants
+  held += 24 * O3 * 18;                      // apply + eval kernel sets, FP64 + FP32
+  // set-up peak: oversampled (3n)^3 and (2n)^3 FP64 transform buffers
+  const size_t setup = held + 16 * (27 * N + 8 * N);
+  // steady state: FP64 apply workspace, mixed-precision Krylov group
+  size_t steady = held + apply_workspace_bytes(n, c, nrhs, VIE_FP64);
+  steady += (size_t)nrhs * c * N * (8 * (size_t)(restart + 1) + 16 * 2 + 8);
+  return setup > steady ? setup : steady;
+}
+
+vie_status vie_tune(vie_problem* P, int precision, int* variant, void* stream) {
+  if (!P || !variant || (precision != VIE_FP64 && precision != VIE_FP32)) {
+    set_error("vie_tune: bad argument");
+    return VIE_EINVAL;
+  }
+  return tune_apply(P, P->kapply, precision, variant, (cudaStream_t)stream);
 }
 
 vie_status vie_profile_begin(vie_problem* P, int cap) {

@@ -89,14 +89,13 @@ vie_status run_rhs(vie_problem* P, const double* d, const double* p, int nrhs, v
 }
 
 // ------------------------------------------------------------ vector ops
+// Right-hand sides are solved in lockstep groups of nb: every Arnoldi step is
+// one batched operator apply over the group and one batched reduction, with a
+// single device-to-host copy of all the group's Hessenberg columns.  Device
+// layout of a group: vectors [r][L] (r < nb); Krylov basis [i][r][L].
 static const int kRedBlocks = 304;  // 2 x 152 SMs
 static const int kRedThreads = 256;
 static const int kDotChunk = 8;
-
-template <typename V>
-__device__ __forceinline__ double2 to_d(V a) {
-  return make_double2((double)a.x, (double)a.y);
-}
 
 // Per-thread accumulation type: FP64 for an FP64 basis; FP32 for an FP32
 // basis (each thread sums only ~L / 77824 terms in FP32 before the FP64
@@ -106,15 +105,17 @@ template <typename TB> struct Acc;
 template <> struct Acc<double2> { typedef double T; typedef double2 V; };
 template <> struct Acc<float2> { typedef float T; typedef float2 V; };
 
-// partial[i * G + block] = sum over this block's elements of conj(V_i) w, i < k;
-// if with_self, slot k also gets conj(w) w.
+// partial[(r * ldp + i) * G + block] = block's share of conj(V_i[r]) w[r], i < k;
+// with_self: slot k gets conj(w[r]) w[r].  grid = (G, nb).
 template <typename TB>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__ Vb, long long ldv, int k,
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__ V, long long ldi, int k,
                                                           const TB* __restrict__ w, long long L, double2* partial,
-                                                          int with_self) {
+                                                          int ldp, int with_self) {
   typedef typename Acc<TB>::T AT;
   __shared__ double2 red[kRedThreads / 32][kDotChunk];
-  const int G = gridDim.x;
+  const int G = gridDim.x, r = blockIdx.y;
+  const TB* Vr = V + (long long)r * L;
+  const TB* wr = w + (long long)r * L;
   const int ktot = k + (with_self ? 1 : 0);
   for (int i0 = 0; i0 < ktot; i0 += kDotChunk) {
     const int cnt = min(kDotChunk, ktot - i0);
@@ -122,12 +123,12 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__
 #pragma unroll
     for (int t = 0; t < kDotChunk; ++t) ar[t] = ai[t] = (AT)0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)G * blockDim.x) {
-      const TB we = w[e];
+      const TB we = wr[e];
 #pragma unroll
       for (int t = 0; t < kDotChunk; ++t)
         if (t < cnt) {
           const int i = i0 + t;
-          const TB v = (i < k) ? Vb[(long long)i * ldv + e] : we;
+          const TB v = (i < k) ? Vr[(long long)i * ldi + e] : we;
           ar[t] += v.x * we.x + v.y * we.y;
           ai[t] += v.x * we.y - v.y * we.x;
         }
@@ -145,17 +146,19 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__
     if (threadIdx.x < cnt) {
       double2 sm = make_double2(0, 0);
       for (int wgi = 0; wgi < kRedThreads / 32; ++wgi) sm = sm + red[wgi][threadIdx.x];
-      partial[(long long)(i0 + threadIdx.x) * G + blockIdx.x] = sm;
+      partial[((long long)r * ldp + i0 + threadIdx.x) * G + blockIdx.x] = sm;
     }
     __syncthreads();
   }
 }
 
-__global__ void k_reduce_partials(const double2* __restrict__ partial, int k, int G, double2* __restrict__ out) {
-  const int i = blockIdx.x;
+// out[r * ldo + i] = sum_b partial[(r * ldp + i) * G + b], grid = (k, nb).
+__global__ void k_reduce_partials(const double2* __restrict__ partial, int k, int G, int ldp,
+                                  double2* __restrict__ out, int ldo) {
+  const int i = blockIdx.x, r = blockIdx.y;
   if (i >= k) return;
   double2 s = make_double2(0, 0);
-  for (int b = threadIdx.x; b < G; b += blockDim.x) s = s + partial[(long long)i * G + b];
+  for (int b = threadIdx.x; b < G; b += blockDim.x) s = s + partial[((long long)r * ldp + i) * G + b];
   __shared__ double2 red[32];
   for (int off = 16; off > 0; off >>= 1) {
     s.x += __shfl_down_sync(0xffffffffu, s.x, off);
@@ -166,78 +169,87 @@ __global__ void k_reduce_partials(const double2* __restrict__ partial, int k, in
   if (threadIdx.x == 0) {
     double2 t = make_double2(0, 0);
     for (int j = 0; j < (int)(blockDim.x + 31) / 32; ++j) t = t + red[j];
-    out[i] = t;
+    out[(long long)r * ldo + i] = t;
   }
 }
 
-// w -= sum_i coef[i] V_i (coef on the device); if norm_partial, also the
-// block partial sums of |w|^2 after the update (slot blockIdx.x).
+// w[r] -= sum_i coef[r * ldc + i] V_i[r]; block partial sums of |w[r]|^2 to
+// partial[r * ldp * G + block].  grid = (G, nb).
 template <typename TB>
-__global__ void __launch_bounds__(kRedThreads) k_axpy_norm(TB* __restrict__ w, const TB* __restrict__ Vb, long long ldv,
-                                                           int k, const double2* __restrict__ coef, long long L,
-                                                           double2* norm_partial) {
+__global__ void __launch_bounds__(kRedThreads) k_axpy_norm(TB* __restrict__ w, const TB* __restrict__ V, long long ldi,
+                                                           int k, const double2* __restrict__ coef, int ldc,
+                                                           long long L, double2* partial, int ldp) {
   typedef typename Acc<TB>::T AT;
   __shared__ typename Acc<TB>::V cs[256];
   __shared__ double red[kRedThreads / 32];
+  const int r = blockIdx.y;
   for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) {
-    cs[i].x = (AT)coef[i].x;
-    cs[i].y = (AT)coef[i].y;
+    cs[i].x = (AT)coef[(long long)r * ldc + i].x;
+    cs[i].y = (AT)coef[(long long)r * ldc + i].y;
   }
   __syncthreads();
+  TB* wr = w + (long long)r * L;
+  const TB* Vr = V + (long long)r * L;
   AT nn = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
-    TB acc = w[e];
+    TB acc = wr[e];
     for (int i = 0; i < k; ++i) {
-      const TB v = Vb[(long long)i * ldv + e];
+      const TB v = Vr[(long long)i * ldi + e];
       const typename Acc<TB>::V c = cs[i];
       acc.x -= c.x * v.x - c.y * v.y;
       acc.y -= c.x * v.y + c.y * v.x;
     }
-    w[e] = acc;
+    wr[e] = acc;
     nn += acc.x * acc.x + acc.y * acc.y;
   }
-  if (norm_partial) {
-    double d = (double)nn;
-    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int j = 0; j < kRedThreads / 32; ++j) t += red[j];
-      norm_partial[blockIdx.x] = make_double2(t, 0.0);
-    }
+  double d = (double)nn;
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int j = 0; j < kRedThreads / 32; ++j) t += red[j];
+    partial[(long long)r * ldp * gridDim.x + blockIdx.x] = make_double2(t, 0.0);
   }
 }
 
-// x += sum_i coef[i] V_i with x FP64 and V of type TB (products in TB's precision).
+// x[r] += sum_i coef[r * ldc + i] V_i[r]  (x FP64, products in TB's precision).  grid = (blocks, nb).
 template <typename TB>
-__global__ void k_update(double2* __restrict__ x, const TB* __restrict__ Vb, long long ldv, int k,
-                         const double2* __restrict__ coef, long long L) {
+__global__ void k_update(double2* __restrict__ x, const TB* __restrict__ V, long long ldi, int k,
+                         const double2* __restrict__ coef, int ldc, long long L) {
   typedef typename Acc<TB>::T AT;
   __shared__ typename Acc<TB>::V cs[256];
+  const int r = blockIdx.y;
   for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) {
-    cs[i].x = (AT)coef[i].x;
-    cs[i].y = (AT)coef[i].y;
+    cs[i].x = (AT)coef[(long long)r * ldc + i].x;
+    cs[i].y = (AT)coef[(long long)r * ldc + i].y;
   }
   __syncthreads();
+  double2* xr = x + (long long)r * L;
+  const TB* Vr = V + (long long)r * L;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
     AT ax = 0, ay = 0;
     for (int i = 0; i < k; ++i) {
-      const TB v = Vb[(long long)i * ldv + e];
+      const TB v = Vr[(long long)i * ldi + e];
       ax += cs[i].x * v.x - cs[i].y * v.y;
       ay += cs[i].x * v.y + cs[i].y * v.x;
     }
-    x[e].x += (double)ax;
-    x[e].y += (double)ay;
+    xr[e].x += (double)ax;
+    xr[e].y += (double)ay;
   }
 }
 
-// dst = scale * src (types may differ)
+// dst[r] = scale[r] * src[r] (types may differ).  grid = (blocks, nb).
 template <typename TD, typename TS>
-__global__ void k_scale(TD* __restrict__ dst, const TS* __restrict__ src, double scale, long long L) {
+__global__ void k_scale(TD* __restrict__ dst, const TS* __restrict__ src, const double* __restrict__ scale,
+                        long long L) {
+  const int r = blockIdx.y;
+  const double sc = scale[r];
+  TD* d = dst + (long long)r * L;
+  const TS* s = src + (long long)r * L;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
-    dst[e].x = scale * (double)src[e].x;
-    dst[e].y = scale * (double)src[e].y;
+    d[e].x = sc * (double)s[e].x;
+    d[e].y = sc * (double)s[e].y;
   }
 }
 
@@ -249,149 +261,187 @@ __global__ void k_bminus(double2* __restrict__ r, const double2* __restrict__ b,
 
 static int ew_blocks(long long L) { return (int)std::min<long long>((L + 255) / 256, 152LL * 8); }
 
-struct KrylovBufs {
-  double2* partial = nullptr;  // [(m+2) * G]
-  double2* hdev = nullptr;     // [2 (m+3)]
-  double2* r = nullptr;        // FP64 residual / work
-  double2* w64 = nullptr;      // FP64 Arnoldi vector
-  float2* w32 = nullptr;       // FP32 Arnoldi vector
-  void* V = nullptr;           // basis (m+1) x L, FP64 or FP32
+struct Group {
+  int nb = 1;
+  int m = 1;
+  long long L = 0;
+  double2* partial = nullptr;  // [nb][m+3][G]
+  double2* hdev = nullptr;     // [nb][HS]
+  double* sdev = nullptr;      // [nb] scales
+  double2* r = nullptr;        // [nb][L] FP64
+  double2* w64 = nullptr;      // [nb][L]
+  float2* w32 = nullptr;       // [nb][L]
+  void* V = nullptr;           // [m+1][nb][L]
+  int HS = 0;                  // stride of hdev per rhs
 };
 
-// h[0..k-1] = V^H w (+ slot k = |w|^2 if with_self), left on the device in kb.hdev + off.
-template <typename TB>
-static vie_status dots_dev(const TB* V, long long L, int k, const TB* w, bool with_self, KrylovBufs& kb, int off,
-                           cudaStream_t st) {
-  const int kt = k + (with_self ? 1 : 0);
-  k_multidot<TB><<<kRedBlocks, kRedThreads, 0, st>>>(V, L, k, w, L, kb.partial, with_self ? 1 : 0);
-  VIE_CK(cudaGetLastError());
-  k_reduce_partials<<<kt, 256, 0, st>>>(kb.partial, kt, kRedBlocks, kb.hdev + off);
-  VIE_CK(cudaGetLastError());
-  return VIE_OK;
-}
+static int ldp_of(const Group& g) { return g.m + 3; }
 
-// w -= V h (h at kb.hdev + hoff on the device); |w|^2 to kb.hdev + noff.
-template <typename TB>
-static vie_status axpy_norm_dev(TB* w, const TB* V, long long L, int k, KrylovBufs& kb, int hoff, int noff,
-                                cudaStream_t st) {
-  k_axpy_norm<TB><<<kRedBlocks, kRedThreads, 0, st>>>(w, V, L, k, kb.hdev + hoff, L, kb.partial);
+// norms of nb vectors [r][L] (FP64) -> host
+static vie_status norms_host(const double2* v, Group& g, std::vector<double>& out, cudaStream_t st) {
+  k_multidot<double2><<<dim3(kRedBlocks, g.nb), kRedThreads, 0, st>>>(v, 0, 0, v, g.L, g.partial, ldp_of(g), 1);
   VIE_CK(cudaGetLastError());
-  k_reduce_partials<<<1, 256, 0, st>>>(kb.partial, 1, kRedBlocks, kb.hdev + noff);
+  k_reduce_partials<<<dim3(1, g.nb), 256, 0, st>>>(g.partial, 1, kRedBlocks, ldp_of(g), g.hdev, g.HS);
   VIE_CK(cudaGetLastError());
-  return VIE_OK;
-}
-
-static vie_status norm2(const double2* v, long long L, KrylovBufs& kb, double* out, cudaStream_t st) {
-  vie_status s = dots_dev<double2>(v, L, 1, v, false, kb, 0, st);
-  if (s != VIE_OK) return s;
-  double2 h;
-  VIE_CK(cudaMemcpyAsync(&h, kb.hdev, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  std::vector<double2> h((size_t)g.nb * g.HS);
+  VIE_CK(cudaMemcpyAsync(h.data(), g.hdev, sizeof(double2) * g.nb * g.HS, cudaMemcpyDeviceToHost, st));
   VIE_CK(cudaStreamSynchronize(st));
-  *out = std::sqrt(std::max(0.0, h.x));
+  out.resize(g.nb);
+  for (int r = 0; r < g.nb; ++r) out[r] = std::sqrt(std::max(0.0, h[(size_t)r * g.HS].x));
   return VIE_OK;
 }
 
-// One GMRES(m) cycle on the operator applied in the precision of TB (basis
-// type TB).  Arnoldi by classical Gram-Schmidt with one device-resident
-// reduction per step and a second pass only when the projection removed
-// more than 3/4 of the norm (Kahan-Parlett "twice is enough").
-//   rhs r (FP64, norm beta); result x (FP64) += V y.
+// One GMRES(m) cycle for the whole group on the operator applied in the
+// precision of TB (basis type TB).  Arnoldi: classical Gram-Schmidt, one
+// device reduction per step (inner products and |w|^2 in one pass, the update
+// and |w'|^2 in a second), a second Gram-Schmidt pass when the first removed
+// more than 3/4 of some member's norm (Kahan-Parlett "twice is enough").
+//   r (FP64 residuals, norms beta[r]); x (FP64) += V y.  Members with
+//   beta = 0 ride along with zero vectors.  Returns steps per member.
 template <typename TB>
-static vie_status gmres_cycle(vie_problem* P, const double2* r, double beta, double2* x, int m, double stop_abs,
-                              KrylovBufs& kb, int* steps, double* est, int* applies, cudaStream_t st) {
-  const long long L = (long long)P->ncomp * P->n * P->n * P->n;
-  TB* V = (TB*)kb.V;
-  TB* w = (TB*)(sizeof(TB) == sizeof(double2) ? (void*)kb.w64 : (void*)kb.w32);
+static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double>& beta, double2* x,
+                              const std::vector<double>& stop_abs, std::vector<int>& steps, int* applies,
+                              cudaStream_t st) {
+  const long long L = g.L;
+  const int nb = g.nb, m = g.m, HS = g.HS, ldp = ldp_of(g);
+  const long long ldi = (long long)nb * L;
+  TB* V = (TB*)g.V;
+  TB* w = (TB*)(sizeof(TB) == sizeof(double2) ? (void*)g.w64 : (void*)g.w32);
   const int prec = sizeof(TB) == sizeof(double2) ? VIE_FP64 : VIE_FP32;
-  k_scale<TB, double2><<<ew_blocks(L), 256, 0, st>>>(V, r, 1.0 / beta, L);
+  const dim3 ewg(ew_blocks(L), nb), redg(kRedBlocks, nb);
+  std::vector<double> sc(nb);
+  for (int r = 0; r < nb; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+  VIE_CK(cudaMemcpyAsync(g.sdev, sc.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+  k_scale<TB, double2><<<ewg, 256, 0, st>>>(V, g.r, g.sdev, L);
   VIE_CK(cudaGetLastError());
-  std::vector<cd> Hm((size_t)(m + 1) * m, cd(0, 0)), cs(m), sn(m), g(m + 1, cd(0, 0));
-  g[0] = beta;
-  int j = 0;
-  std::vector<double2> hb(2 * (m + 3));
-  *est = beta;
-  const int H2 = m + 3;  // offset of the second-pass coefficients in hdev
-  for (; j < m; ++j) {
-    vie_status s = run_apply(P, P->kapply, V + (long long)j * L, w, prec, 1, true, st);
+  std::vector<cd> Hm((size_t)nb * (m + 1) * m, cd(0, 0)), cs((size_t)nb * m), sn((size_t)nb * m),
+      gg((size_t)nb * (m + 1), cd(0, 0));
+  std::vector<char> done(nb, 0);
+  steps.assign(nb, 0);
+  int active = 0;
+  for (int r = 0; r < nb; ++r) {
+    gg[(size_t)r * (m + 1)] = beta[r];
+    if (beta[r] <= stop_abs[r] || beta[r] == 0.0) done[r] = 1;
+    else ++active;
+  }
+  std::vector<double2> hb((size_t)nb * HS);
+  const int H2 = m + 3;  // second-pass slot offset inside a member's hdev row
+  for (int j = 0; j < m && active > 0; ++j) {
+    vie_status s = run_apply(P, P->kapply, V + (long long)j * ldi, w, prec, nb, true, st);
     if (s != VIE_OK) return s;
-    ++*applies;
-    s = dots_dev<TB>(V, L, j + 1, w, true, kb, 0, st);  // h, |w|^2 at slot j+1
-    if (s != VIE_OK) return s;
-    s = axpy_norm_dev<TB>(w, V, L, j + 1, kb, 0, j + 2, st);  // |w'|^2 at slot j+2
-    if (s != VIE_OK) return s;
-    VIE_CK(cudaMemcpyAsync(hb.data(), kb.hdev, sizeof(double2) * (j + 3), cudaMemcpyDeviceToHost, st));
-    VIE_CK(cudaStreamSynchronize(st));
-    std::vector<cd> h(j + 1);
-    for (int i = 0; i <= j; ++i) h[i] = cd(hb[i].x, hb[i].y);
-    const double w0 = hb[j + 1].x;
-    double wn2 = hb[j + 2].x;
-    if (wn2 < 0.0625 * w0) {
-      // second Gram-Schmidt pass
-      s = dots_dev<TB>(V, L, j + 1, w, false, kb, H2, st);
-      if (s != VIE_OK) return s;
-      s = axpy_norm_dev<TB>(w, V, L, j + 1, kb, H2, H2 + j + 1, st);
-      if (s != VIE_OK) return s;
-      VIE_CK(cudaMemcpyAsync(hb.data() + H2, kb.hdev + H2, sizeof(double2) * (j + 2), cudaMemcpyDeviceToHost, st));
-      VIE_CK(cudaStreamSynchronize(st));
-      for (int i = 0; i <= j; ++i) h[i] += cd(hb[H2 + i].x, hb[H2 + i].y);
-      wn2 = hb[H2 + j + 1].x;
-    }
-    const double hn = std::sqrt(std::max(0.0, wn2));
-    if (!std::isfinite(hn) || !std::isfinite(w0)) {
-      set_error("non-finite value in the Arnoldi process");
-      return VIE_ENAN;
-    }
-    for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] = h[i];
-    Hm[(size_t)(j + 1) * m + j] = hn;
-    for (int i = 0; i < j; ++i) {
-      const cd a = Hm[(size_t)i * m + j], bb = Hm[(size_t)(i + 1) * m + j];
-      Hm[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
-      Hm[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
-    }
-    const cd a = Hm[(size_t)j * m + j], bb = Hm[(size_t)(j + 1) * m + j];
-    const double den = std::sqrt(std::norm(a) + std::norm(bb));
-    cs[j] = den > 0 ? a / den : cd(1, 0);
-    sn[j] = den > 0 ? bb / den : cd(0, 0);
-    Hm[(size_t)j * m + j] = std::conj(cs[j]) * a + std::conj(sn[j]) * bb;
-    Hm[(size_t)(j + 1) * m + j] = 0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = std::conj(cs[j]) * g[j];
-    *est = std::abs(g[j + 1]);
-    if (*est <= stop_abs || hn == 0.0 || j + 1 == m) {
-      ++j;
-      break;
-    }
-    k_scale<TB, TB><<<ew_blocks(L), 256, 0, st>>>(V + (long long)(j + 1) * L, w, 1.0 / hn, L);
+    *applies += active;
+    k_multidot<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j + 1, w, L, g.partial, ldp, 1);
     VIE_CK(cudaGetLastError());
+    k_reduce_partials<<<dim3(j + 2, nb), 256, 0, st>>>(g.partial, j + 2, kRedBlocks, ldp, g.hdev, HS);
+    VIE_CK(cudaGetLastError());
+    k_axpy_norm<TB><<<redg, kRedThreads, 0, st>>>(w, V, ldi, j + 1, g.hdev, HS, L, g.partial, ldp);
+    VIE_CK(cudaGetLastError());
+    k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, kRedBlocks, ldp, g.hdev + (j + 2), HS);
+    VIE_CK(cudaGetLastError());
+    VIE_CK(cudaMemcpyAsync(hb.data(), g.hdev, sizeof(double2) * nb * HS, cudaMemcpyDeviceToHost, st));
+    VIE_CK(cudaStreamSynchronize(st));
+    bool reorth = false;
+    for (int r = 0; r < nb; ++r)
+      if (!done[r] && hb[(size_t)r * HS + j + 2].x < 0.0625 * hb[(size_t)r * HS + j + 1].x) reorth = true;
+    if (reorth) {
+      k_multidot<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j + 1, w, L, g.partial, ldp, 0);
+      VIE_CK(cudaGetLastError());
+      k_reduce_partials<<<dim3(j + 1, nb), 256, 0, st>>>(g.partial, j + 1, kRedBlocks, ldp, g.hdev + H2, HS);
+      VIE_CK(cudaGetLastError());
+      k_axpy_norm<TB><<<redg, kRedThreads, 0, st>>>(w, V, ldi, j + 1, g.hdev + H2, HS, L, g.partial, ldp);
+      VIE_CK(cudaGetLastError());
+      k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, kRedBlocks, ldp, g.hdev + H2 + j + 1, HS);
+      VIE_CK(cudaGetLastError());
+      VIE_CK(cudaMemcpyAsync(hb.data(), g.hdev, sizeof(double2) * nb * HS, cudaMemcpyDeviceToHost, st));
+      VIE_CK(cudaStreamSynchronize(st));
+    }
+    for (int r = 0; r < nb; ++r) {
+      sc[r] = 0.0;
+      if (done[r]) continue;
+      const double2* hr = &hb[(size_t)r * HS];
+      const double w0 = hr[j + 1].x;
+      double wn2 = reorth ? hr[H2 + j + 1].x : hr[j + 2].x;
+      const double hn = std::sqrt(std::max(0.0, wn2));
+      if (!std::isfinite(hn) || !std::isfinite(w0)) {
+        set_error("non-finite value in the Arnoldi process");
+        return VIE_ENAN;
+      }
+      cd* H = &Hm[(size_t)r * (m + 1) * m];
+      cd* c_ = &cs[(size_t)r * m];
+      cd* s_ = &sn[(size_t)r * m];
+      cd* g_ = &gg[(size_t)r * (m + 1)];
+      for (int i = 0; i <= j; ++i) {
+        cd h(hr[i].x, hr[i].y);
+        if (reorth) h += cd(hr[H2 + i].x, hr[H2 + i].y);
+        H[(size_t)i * m + j] = h;
+      }
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const cd a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = std::conj(c_[i]) * a + std::conj(s_[i]) * bb;
+        H[(size_t)(i + 1) * m + j] = -s_[i] * a + c_[i] * bb;
+      }
+      const cd a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      const double den = std::sqrt(std::norm(a) + std::norm(bb));
+      c_[j] = den > 0 ? a / den : cd(1, 0);
+      s_[j] = den > 0 ? bb / den : cd(0, 0);
+      H[(size_t)j * m + j] = std::conj(c_[j]) * a + std::conj(s_[j]) * bb;
+      H[(size_t)(j + 1) * m + j] = 0;
+      g_[j + 1] = -s_[j] * g_[j];
+      g_[j] = std::conj(c_[j]) * g_[j];
+      steps[r] = j + 1;
+      if (std::abs(g_[j + 1]) <= stop_abs[r] || hn == 0.0) {
+        done[r] = 1;
+        --active;
+      } else {
+        sc[r] = 1.0 / hn;
+      }
+    }
+    if (j + 1 < m && active > 0) {
+      VIE_CK(cudaMemcpyAsync(g.sdev, sc.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+      k_scale<TB, TB><<<ewg, 256, 0, st>>>(V + (long long)(j + 1) * ldi, w, g.sdev, L);
+      VIE_CK(cudaGetLastError());
+    }
   }
-  // back substitution R y = g
-  std::vector<cd> y(j);
-  for (int i = j - 1; i >= 0; --i) {
-    cd acc = g[i];
-    for (int q = i + 1; q < j; ++q) acc -= Hm[(size_t)i * m + q] * y[q];
-    y[i] = acc / Hm[(size_t)i * m + i];
+  // back substitution R y = g per member; coefficients to the device, x += V y
+  int kmax = 0;
+  for (int r = 0; r < nb; ++r) kmax = std::max(kmax, steps[r]);
+  if (kmax == 0) return VIE_OK;
+  std::vector<cd> y((size_t)nb * HS, cd(0, 0));
+  for (int r = 0; r < nb; ++r) {
+    const int jr = steps[r];
+    const cd* H = &Hm[(size_t)r * (m + 1) * m];
+    const cd* g_ = &gg[(size_t)r * (m + 1)];
+    cd* yr = &y[(size_t)r * HS];
+    for (int i = jr - 1; i >= 0; --i) {
+      cd acc = g_[i];
+      for (int q = i + 1; q < jr; ++q) acc -= H[(size_t)i * m + q] * yr[q];
+      yr[i] = acc / H[(size_t)i * m + i];
+    }
   }
-  VIE_CK(cudaMemcpyAsync(kb.hdev, y.data(), sizeof(double2) * j, cudaMemcpyHostToDevice, st));
-  k_update<TB><<<ew_blocks(L), 256, 0, st>>>(x, V, L, j, kb.hdev, L);
+  VIE_CK(cudaMemcpyAsync(g.hdev, y.data(), sizeof(double2) * nb * HS, cudaMemcpyHostToDevice, st));
+  k_update<TB><<<ewg, 256, 0, st>>>(x, V, ldi, kmax, g.hdev, HS, L);
   VIE_CK(cudaGetLastError());
   VIE_CK(cudaStreamSynchronize(st));  // y is a host temporary
-  *steps = j;
   return VIE_OK;
 }
 
-static vie_status ensure_krylov(vie_problem* P, int m, bool mixed, KrylovBufs& kb) {
-  const long long L = (long long)P->ncomp * P->n * P->n * P->n;
+// Bytes of Krylov workspace per right-hand side.
+static size_t group_bytes_per_rhs(long long L, int m, bool mixed) {
   const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
-  const size_t need = sizeof(double2) * ((size_t)(m + 2) * kRedBlocks + 2 * (m + 3)) + sizeof(double2) * 2 * L +
-                      sizeof(float2) * L + esz * (size_t)(m + 1) * L + 4096;
+  return esz * (size_t)(m + 1) * L + sizeof(double2) * 2 * L + sizeof(float2) * L +
+         sizeof(double2) * ((size_t)(m + 3) * kRedBlocks + 2 * (m + 4)) + 64;
+}
+
+static vie_status ensure_group(vie_problem* P, int m, bool mixed, int nb, Group& g, cudaStream_t st) {
+  const long long L = (long long)P->ncomp * P->n * P->n * P->n;
+  const size_t need = group_bytes_per_rhs(L, m, mixed) * nb + 16 * 4096;
   if (P->ks.bytes < need) {
-    if (P->ks.buf) {
-      cudaDeviceSynchronize();
-      cudaFree(P->ks.buf);
-      P->ks.buf = nullptr;
-      P->ks.bytes = 0;
-    }
-    if (cudaMalloc(&P->ks.buf, need) != cudaSuccess) {
+    dfree(P->ks.buf, st);
+    P->ks.buf = nullptr;
+    P->ks.bytes = 0;
+    if (dalloc(&P->ks.buf, need, st) != cudaSuccess) {
+      cudaGetLastError();
       set_error("out of device memory for the Krylov basis");
       return VIE_ENOMEM;
     }
@@ -403,13 +453,35 @@ static vie_status ensure_krylov(vie_problem* P, int m, bool mixed, KrylovBufs& k
     p += (bytes + 255) & ~(size_t)255;
     return (void*)q;
   };
-  kb.partial = (double2*)take(sizeof(double2) * (size_t)(m + 2) * kRedBlocks);
-  kb.hdev = (double2*)take(sizeof(double2) * 2 * (m + 3));
-  kb.r = (double2*)take(sizeof(double2) * L);
-  kb.w64 = (double2*)take(sizeof(double2) * L);
-  kb.w32 = (float2*)take(sizeof(float2) * L);
-  kb.V = take(esz * (size_t)(m + 1) * L);
+  const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
+  g.nb = nb;
+  g.m = m;
+  g.L = L;
+  g.HS = 2 * (m + 4);
+  g.partial = (double2*)take(sizeof(double2) * (size_t)nb * (m + 3) * kRedBlocks);
+  g.hdev = (double2*)take(sizeof(double2) * (size_t)nb * g.HS);
+  g.sdev = (double*)take(sizeof(double) * nb);
+  g.r = (double2*)take(sizeof(double2) * (size_t)nb * L);
+  g.w64 = (double2*)take(sizeof(double2) * (size_t)nb * L);
+  g.w32 = (float2*)take(sizeof(float2) * (size_t)nb * L);
+  g.V = take(esz * (size_t)(m + 1) * nb * L);
   return VIE_OK;
+}
+
+// Lockstep group size: every right-hand side at once if the Krylov basis and
+// the batched FP64 apply workspace fit in 80% of free device memory.
+static int pick_group(vie_problem* P, int nrhs, int m, bool mixed) {
+  const long long L = (long long)P->ncomp * P->n * P->n * P->n;
+  size_t freeb = 0, totb = 0;
+  if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) return 1;
+  freeb += P->ks.bytes + P->ws.bytes;  // our own workspaces are reusable
+  const size_t per = group_bytes_per_rhs(L, m, mixed) +
+                     apply_workspace_bytes(P->n, std::max(cin_of(P->kapply.mode), cout_of(P->kapply.mode)), 1,
+                                           VIE_FP64);
+  long long nb = (long long)(0.8 * (double)freeb / (double)per);
+  const char* cap = getenv("VIE_GROUP_MAX");
+  if (cap) nb = std::min<long long>(nb, atoi(cap));
+  return (int)std::max<long long>(1, std::min<long long>(nb, std::min(nrhs, 64)));
 }
 
 vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_opts* opt, vie_solve_info* info,
@@ -418,75 +490,91 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
   const long long L = (long long)P->ncomp * P->n * P->n * P->n;
   const int m = opt->restart;
   const bool mixed = opt->mode == VIE_SOLVE_MIXED;
-  KrylovBufs kb;
-  vie_status s = ensure_krylov(P, m, mixed, kb);
-  if (s != VIE_OK) return s;
   vie_solve_info inf{};
   vie_status final_status = VIE_OK;
   double worst = 0.0;
-  for (int rr = 0; rr < opt->nrhs; ++rr) {
-    const double2* b = (const double2*)rhs + rr * L;
-    double2* x = (double2*)Jv + rr * L;
-    double nb = 0.0, nx = 0.0;
-    s = norm2(b, L, kb, &nb, st);
+  const int gsz = pick_group(P, opt->nrhs, m, mixed);
+  for (int r0 = 0; r0 < opt->nrhs; r0 += gsz) {
+    const int nb = std::min(gsz, opt->nrhs - r0);
+    Group g;
+    vie_status s = ensure_group(P, m, mixed, nb, g, st);
     if (s != VIE_OK) return s;
-    s = norm2(x, L, kb, &nx, st);
+    const double2* b = (const double2*)rhs + (long long)r0 * L;
+    double2* x = (double2*)Jv + (long long)r0 * L;
+    std::vector<double> nbv, nxv, beta(nb), rel(nb, 1.0);
+    s = norms_host(b, g, nbv, st);
     if (s != VIE_OK) return s;
-    if (!(nb > 0.0) || !std::isfinite(nb)) {
-      if (nb == 0.0) {
-        VIE_CK(cudaMemsetAsync(x, 0, sizeof(double2) * L, st));
-        continue;
+    s = norms_host(x, g, nxv, st);
+    if (s != VIE_OK) return s;
+    bool x_zero = true;
+    for (int r = 0; r < nb; ++r) {
+      if (!std::isfinite(nbv[r])) {
+        set_error("non-finite right-hand side");
+        return VIE_ENAN;
       }
-      set_error("non-finite right-hand side");
-      return VIE_ENAN;
+      if (nbv[r] == 0.0 && nxv[r] != 0.0) {
+        // b = 0 has the unique solution J = 0
+        VIE_CK(cudaMemsetAsync(x + (long long)r * L, 0, sizeof(double2) * L, st));
+        nxv[r] = 0.0;
+      }
+      if (nxv[r] != 0.0) x_zero = false;
     }
-    double rel = 1.0;
-    bool conv = false;
+    std::vector<char> conv(nb, 0);
     int total_inner = 0;
     const int max_outer = mixed ? opt->max_outer : std::max(1, opt->max_outer);
     for (int outer = 0; outer <= max_outer; ++outer) {
-      // FP64 residual r = b - A x (r = b for a zero initial guess)
-      double beta = 0.0;
-      if (outer == 0 && nx == 0.0) {
-        VIE_CK(cudaMemcpyAsync(kb.r, b, sizeof(double2) * L, cudaMemcpyDeviceToDevice, st));
-        beta = nb;
+      // FP64 residuals r = b - A x (r = b for zero initial guesses)
+      if (outer == 0 && x_zero) {
+        VIE_CK(cudaMemcpyAsync(g.r, b, sizeof(double2) * nb * L, cudaMemcpyDeviceToDevice, st));
+        beta = nbv;
       } else {
-        s = run_apply(P, P->kapply, x, kb.r, VIE_FP64, 1, true, st);
+        s = run_apply(P, P->kapply, x, g.r, VIE_FP64, nb, true, st);
         if (s != VIE_OK) return s;
-        ++inf.applies_fp64;
-        k_bminus<<<ew_blocks(L), 256, 0, st>>>(kb.r, b, L);
+        inf.applies_fp64 += nb;
+        k_bminus<<<ew_blocks(L * nb), 256, 0, st>>>(g.r, b, L * nb);
         VIE_CK(cudaGetLastError());
-        s = norm2(kb.r, L, kb, &beta, st);
+        s = norms_host(g.r, g, beta, st);
         if (s != VIE_OK) return s;
       }
-      if (!std::isfinite(beta)) {
-        set_error("non-finite residual");
-        return VIE_ENAN;
+      bool all = true;
+      std::vector<double> stop(nb), bx(nb);
+      for (int r = 0; r < nb; ++r) {
+        if (!std::isfinite(beta[r])) {
+          set_error("non-finite residual");
+          return VIE_ENAN;
+        }
+        rel[r] = nbv[r] > 0 ? beta[r] / nbv[r] : 0.0;
+        conv[r] = rel[r] <= opt->tol;
+        if (!conv[r]) all = false;
+        // converged members ride along with zero vectors
+        bx[r] = conv[r] ? 0.0 : beta[r];
+        stop[r] = mixed ? opt->inner_tol * beta[r] : 0.5 * opt->tol * nbv[r];
       }
-      rel = beta / nb;
-      if (rel <= opt->tol) {
-        conv = true;
-        break;
-      }
-      if (outer == max_outer || total_inner >= opt->max_inner) break;
-      int steps = 0;
-      double est = 0.0;
+      if (all || outer == max_outer || total_inner >= opt->max_inner) break;
+      std::vector<int> steps;
       int ap = 0;
-      const int mm = std::min(m, opt->max_inner - total_inner);
+      g.m = std::min(m, opt->max_inner - total_inner);
       if (mixed) {
-        s = gmres_cycle<float2>(P, kb.r, beta, x, mm, opt->inner_tol * beta, kb, &steps, &est, &ap, st);
+        s = gmres_cycle<float2>(P, g, bx, x, stop, steps, &ap, st);
         inf.applies_fp32 += ap;
       } else {
-        s = gmres_cycle<double2>(P, kb.r, beta, x, mm, 0.5 * opt->tol * nb, kb, &steps, &est, &ap, st);
+        s = gmres_cycle<double2>(P, g, bx, x, stop, steps, &ap, st);
         inf.applies_fp64 += ap;
       }
+      g.m = m;
       if (s != VIE_OK) return s;
-      total_inner += steps;
+      int smax = 0;
+      for (int r = 0; r < nb; ++r) {
+        smax = std::max(smax, steps[r]);
+        inf.inner_iters += steps[r];
+      }
+      total_inner += smax;
       ++inf.outer_iters;
     }
-    inf.inner_iters += total_inner;
-    worst = std::max(worst, rel);
-    if (!conv) final_status = VIE_ENOCONV;
+    for (int r = 0; r < nb; ++r) {
+      worst = std::max(worst, rel[r]);
+      if (!conv[r]) final_status = VIE_ENOCONV;
+    }
   }
   VIE_CK(cudaStreamSynchronize(st));
   inf.rel_residual = worst;

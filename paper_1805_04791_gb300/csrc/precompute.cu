@@ -25,8 +25,8 @@ __global__ void k_twiddle(V* tw, int M) {
 }
 
 vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st) {
-  VIE_CK(cudaMalloc(t64, sizeof(double2) * M));
-  VIE_CK(cudaMalloc(t32, sizeof(float2) * M));
+  VIE_CK(dalloc((void**)t64, sizeof(double2) * M, st));
+  VIE_CK(dalloc((void**)t32, sizeof(float2) * M, st));
   k_twiddle<double2><<<(M + 127) / 128, 128, 0, st>>>(*t64, M);
   k_twiddle<float2><<<(M + 127) / 128, 128, 0, st>>>(*t32, M);
   VIE_CK(cudaGetLastError());
@@ -84,15 +84,15 @@ __global__ void k_medium(const double2* __restrict__ eps, double2* __restrict__ 
 
 vie_status build_medium(vie_problem* P, const void* eps, const void* mu, cudaStream_t st) {
   const long long N = (long long)P->n * P->n * P->n;
-  VIE_CK(cudaMalloc(&P->He64, sizeof(double2) * 6 * N));
-  VIE_CK(cudaMalloc(&P->He32, sizeof(float2) * 6 * N));
+  VIE_CK(dalloc((void**)&P->He64, sizeof(double2) * 6 * N, st));
+  VIE_CK(dalloc((void**)&P->He32, sizeof(float2) * 6 * N, st));
   VIE_CK(cudaMemsetAsync(P->dflag, 0, sizeof(int), st));
   const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
   k_medium<<<blocks, 256, 0, st>>>((const double2*)eps, P->He64, P->He32, N, P->kind == VIE_LAPLACE, P->dflag);
   VIE_CK(cudaGetLastError());
   if (P->has_mu) {
-    VIE_CK(cudaMalloc(&P->Hm64, sizeof(double2) * 6 * N));
-    VIE_CK(cudaMalloc(&P->Hm32, sizeof(float2) * 6 * N));
+    VIE_CK(dalloc((void**)&P->Hm64, sizeof(double2) * 6 * N, st));
+    VIE_CK(dalloc((void**)&P->Hm32, sizeof(float2) * 6 * N, st));
     k_medium<<<blocks, 256, 0, st>>>((const double2*)mu, P->Hm64, P->Hm32, N, 0, P->dflag);
     VIE_CK(cudaGetLastError());
   }
@@ -299,8 +299,8 @@ static vie_status combine(vie_problem* P, KernelSet& K, int mode, const CombineD
   const long long O = P->n + 1, O3 = O * O * O;
   K.mode = mode;
   K.narr = cd.narr;
-  VIE_CK(cudaMalloc(&K.oct64, sizeof(double2) * cd.narr * O3));
-  VIE_CK(cudaMalloc(&K.oct32, sizeof(float2) * cd.narr * O3));
+  VIE_CK(dalloc((void**)&K.oct64, sizeof(double2) * cd.narr * O3, st));
+  VIE_CK(dalloc((void**)&K.oct32, sizeof(float2) * cd.narr * O3, st));
   const int blocks = (int)std::min<long long>((O3 + 255) / 256, 152LL * 16);
   k_combine<<<blocks, 256, 0, st>>>(P->sym_oct, K.oct64, K.oct32, O3, cd, diag_add, diag_mask);
   VIE_CK(cudaGetLastError());
@@ -315,12 +315,12 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
   double2* tab = nullptr;
   double2 *F = nullptr, *E = nullptr, *tw_sn = nullptr;
   float2* tw_sn32 = nullptr;
-  VIE_CK(cudaMalloc(&tab, sizeof(double2) * (jmax + 1)));
+  VIE_CK(dalloc((void**)&tab, sizeof(double2) * (jmax + 1), st));
   k_ghat_table<<<(jmax + 256) / 256, 256, 0, st>>>(tab, jmax, dk, w, P->L);
   VIE_CK(cudaGetLastError());
   const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = (long long)(n + 1) * (n + 1) * (n + 1);
-  VIE_CK(cudaMalloc(&F, sizeof(double2) * S3));
-  VIE_CK(cudaMalloc(&E, sizeof(double2) * M3));
+  VIE_CK(dalloc((void**)&F, sizeof(double2) * S3, st));
+  VIE_CK(dalloc((void**)&E, sizeof(double2) * M3, st));
   vie_status s = make_twiddles(sn, &tw_sn, &tw_sn32, st);
   if (s != VIE_OK) return s;
   FftPlan plsn;
@@ -328,7 +328,7 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
     set_error("bad oversampled grid size");
     return VIE_EINVAL;
   }
-  VIE_CK(cudaMalloc(&P->sym_oct, sizeof(double2) * SYM_COUNT * O3));
+  VIE_CK(dalloc((void**)&P->sym_oct, sizeof(double2) * SYM_COUNT * O3, st));
   const bool need1 = P->kind == VIE_MAXWELL;
   const int gb = 152 * 16;
   for (int sym = 0; sym < SYM_COUNT; ++sym) {
@@ -344,12 +344,11 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
     k_octant<<<gb, 256, 0, st>>>(E, P->sym_oct + (long long)sym * O3, n);
     VIE_CK(cudaGetLastError());
   }
-  VIE_CK(cudaStreamSynchronize(st));
-  cudaFree(F);
-  cudaFree(E);
-  cudaFree(tab);
-  cudaFree(tw_sn);
-  cudaFree(tw_sn32);
+  dfree(F, st);
+  dfree(E, st);
+  dfree(tab, st);
+  dfree(tw_sn, st);
+  dfree(tw_sn32, st);
 
   // Fold constants: apply kernels give u with y = x + H u; the 1/(2n)^3 of the
   // inverse DFT is folded in too.

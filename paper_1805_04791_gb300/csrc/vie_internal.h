@@ -69,6 +69,7 @@ struct vie_problem {
   int has_mu = 0;
   double lo = 0, hi = 0, D = 0, h = 0, L = 0, omega = 0;
   int device = 0;
+  cudaStream_t stream = nullptr;  // home stream: memory is freed stream-ordered on it at destroy
   vie::FftPlan plan2n;
   double2* tw64 = nullptr;   // exp(-2 pi i j / 2n), j < 2n
   float2* tw32 = nullptr;
@@ -82,12 +83,17 @@ struct vie_problem {
   vie::Workspace ws;         // padded intermediates
   vie::Workspace ks;         // Krylov workspace
   vie::Profiler prof;
+  int p3_variant[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};  // tuned z-pass variant per (precision, mode)
   int* dflag = nullptr;      // device error flag (NaN, bad input)
 };
 
 namespace vie {
 
 void set_error(const std::string& msg);
+// Stream-ordered device allocation (no device-wide synchronisation, so
+// concurrent problems on other streams keep running).
+cudaError_t dalloc(void** p, size_t bytes, cudaStream_t st);
+void dfree(void* p, cudaStream_t st);
 vie_status cuda_fail(cudaError_t e, const char* what);
 
 #define VIE_CK(call)                                               \
@@ -108,6 +114,8 @@ vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st);
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
                      bool with_identity, cudaStream_t st);
 size_t apply_workspace_bytes(int n, int c, int nrhs, int prec);
+// Pick (by timing, unless VIE_TUNE=0) the z-pass variant for (prec, K.mode); returns it in *variant.
+vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant, cudaStream_t st);
 
 // krylov.cu
 vie_status run_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_opts* opt, vie_solve_info* info,

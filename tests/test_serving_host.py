@@ -1,0 +1,98 @@
+"""Host-side tests of the serving loop and the device medium generator (no GPU).
+
+The admission logic is exercised with a fake solver that sleeps instead of
+launching kernels: the HBM budget and the slot limit must never be exceeded,
+requests are admitted in arrival order, and every request completes.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import vie_inputs as vi
+
+
+def test_serving_mix_is_seeded_and_poisson():
+    a = vi.serving_mix(200, rate_per_s=50.0, seed=3)
+    b = vi.serving_mix(200, rate_per_s=50.0, seed=3)
+    assert [r.arrival_s for r in a] == [r.arrival_s for r in b]
+    assert [(r.kind, r.n, r.seed) for r in a] == [(r.kind, r.n, r.seed) for r in b]
+    gaps = np.diff([0.0] + [r.arrival_s for r in a])
+    assert abs(gaps.mean() - 1 / 50.0) < 0.25 / 50.0  # exponential inter-arrivals, mean 1/rate
+    assert set(r.n for r in a) <= {32, 48, 64, 96, 128, 192}
+    assert {r.kind for r in a} == {"helmholtz", "maxwell"}
+    for r in a:
+        assert 1.0 <= r.wavelengths <= 8.0
+        assert abs(np.linalg.norm(r.direction) - 1) < 1e-12 and abs(r.direction @ r.polarisation) < 1e-12
+
+
+def test_torch_medium_matches_numpy_generator():
+    torch = pytest.importorskip("torch")
+    n, seed = 10, 77
+    e_t = vi.bump_medium_torch(n, seed, torch.device("cpu")).numpy()
+    rng = vi.SplitMix64(seed)
+    e_n = vi.anisotropic_bump(n, -1.0, 1.0, 0.5, 0.1, rng).reshape(9, -1)
+    assert np.max(np.abs(e_t - e_n)) <= 1e-15
+
+
+class FakeServer:
+    """Server with the solve replaced by a sleep; checks the admission invariants."""
+
+    def __init__(self, budget, slots):
+        from paper_1805_04791_gb300 import serve
+
+        self.mod = serve
+        self.budget = budget
+        self.slots = slots
+        self.lock = threading.Lock()
+        self.used = 0
+        self.inflight = 0
+        self.violations = []
+        self.order = []
+
+    def make(self):
+        outer = self
+
+        class S(self.mod.Server):
+            def request_bytes(self, req):
+                return req.n * 1000
+
+            def _solve(self, req, res, done_cb):
+                with outer.lock:
+                    outer.used += req.n * 1000
+                    outer.inflight += 1
+                    outer.order.append(req.rid)
+                    if outer.used > outer.budget or outer.inflight > outer.slots:
+                        outer.violations.append((req.rid, outer.used, outer.inflight))
+                time.sleep(0.002 * req.n / 32)
+                res.status = "ok"
+                res.rel_residual = 0.0
+                with outer.lock:
+                    outer.used -= req.n * 1000
+                    outer.inflight -= 1
+                done_cb(res)
+
+        return S(budget_bytes=self.budget, max_slots=self.slots)
+
+
+def test_admission_respects_budget_and_slots():
+    pytest.importorskip("torch")
+    reqs = vi.serving_mix(60, rate_per_s=2000.0, seed=1)
+    fake = FakeServer(budget=300_000, slots=4)
+    stats = fake.make().run(reqs)
+    assert not fake.violations
+    s = stats.summary()
+    assert s["completed"] == 60 and s["failed"] == 0
+    assert stats.peak_bytes <= 300_000 and stats.peak_slots <= 4
+    assert all(r.done_s >= r.admit_s >= r.arrival_s - 1e-9 for r in stats.results)
+
+
+def test_oversized_request_is_rejected_not_hung():
+    pytest.importorskip("torch")
+    reqs = vi.serving_mix(10, rate_per_s=1000.0, seed=2)
+    fake = FakeServer(budget=100_000, slots=8)  # n >= 128 needs > budget
+    stats = fake.make().run(reqs)
+    for r in stats.results:
+        big = r.n * 1000 > 100_000
+        assert (r.status.startswith("rejected")) == big

@@ -288,3 +288,61 @@ def smooth_sphere_eps(n, eps_s, radius, delta, lo=-1.0, hi=1.0):
     for a in range(3):
         eps[a, a] = 1.0 + (eps_s - 1.0) * s
     return eps
+
+
+# --------------------------------------------------------------------------
+# Device-side generation (serving): the same formula as ``anisotropic_bump``,
+# evaluated with torch on the device so that a request's medium never crosses
+# the host link.  Still input generation only: no method arithmetic.
+# --------------------------------------------------------------------------
+
+
+def bump_medium_torch(n: int, seed: int, device, lo=-1.0, hi=1.0, amp=0.5, width2=0.1, eig=(1.0, 2.0, 3.0)):
+    """[9][n^3] complex128 torch tensor of I + amp exp(-|x|^2/width2) R diag(eig) R^T (R from SplitMix64(seed))."""
+    import torch
+
+    rng = SplitMix64(seed)
+    R = random_rotation(rng)
+    S = R @ np.diag(np.asarray(eig, dtype=np.float64)) @ R.T
+    t = torch.as_tensor(grid_nodes(n, lo, hi), dtype=torch.float64, device=device)
+    r2 = t[:, None, None] ** 2 + t[None, :, None] ** 2 + t[None, None, :] ** 2
+    g = torch.exp(-r2 / width2).reshape(-1)
+    eps = torch.zeros((9, n * n * n), dtype=torch.complex128, device=device)
+    for a in range(3):
+        for b in range(3):
+            eps[3 * a + b] = amp * float(S[a, b]) * g + (1.0 if a == b else 0.0)
+    return eps
+
+
+@dataclass
+class ServeRequest:
+    """One solve request of the serving mix."""
+
+    rid: int
+    arrival_s: float
+    kind: str  # "helmholtz" | "maxwell"
+    n: int
+    wavelengths: float
+    seed: int
+    direction: np.ndarray
+    polarisation: np.ndarray
+
+
+def serving_mix(count: int, rate_per_s: float, seed: int = 0, sizes=(32, 48, 64, 96, 128, 192),
+                wl_range=(1.0, 8.0), lo=-1.0, hi=1.0):
+    """Poisson arrivals at ``rate_per_s``; n uniform over ``sizes``; wavelengths across
+    the box uniform in ``wl_range``; kind Helmholtz / Maxwell (mu = I) 50/50; media from
+    the anisotropic-bump generator with a per-request seed."""
+    rng = SplitMix64(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        u = max(rng.uniform(), 1e-300)
+        t += -math.log(u) / rate_per_s
+        n = sizes[min(len(sizes) - 1, int(rng.uniform() * len(sizes)))]
+        wl = rng.uniform_range(*wl_range)
+        kind = "helmholtz" if rng.uniform() < 0.5 else "maxwell"
+        d = sphere_direction(rng)
+        p, _ = polarisations(d, 2 * math.pi * rng.uniform())
+        out.append(ServeRequest(i, t, kind, n, wl, 1000 + i, d, p))
+    return out
