@@ -62,6 +62,13 @@ def parse():
     ap.add_argument("--solves", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--legs", default="",
+                    help="comma list of extra legs: batched (Maxwell 128^3 with mu, 64 plane waves, lockstep "
+                         "GMRES), maxwell256 (Maxwell 256^3 with mu: mixed vs FP64 time to 1e-8), serve "
+                         "(continuous-batching request mix)")
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--batched-rhs", type=int, default=64)
     ap.add_argument("--case", default=None, choices=["apply"],
                     help="minimal run for profilers: build the problem, run --reps FP32 applies, exit")
     ap.add_argument("--reps", type=int, default=3)
@@ -218,6 +225,102 @@ def run_reference(args):
                              "sample": f"{args.steps} FP64 oracle applies at {n}^3 after untimed set-up"},
             "e2e": {"value": v, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def leg_batched(args, dev):
+    """Maxwell with mu at 128^3 (10 wavelengths), 32 directions x 2 polarisations,
+    FP32-inner GMRES in lockstep groups with FP64 refinement to 1e-8."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    nr = args.batched_rhs
+    n = 128
+    p = vi.maxwell_problem(n=n, wavelengths=10.0, ndirs=max(1, nr // 2), npol=2, with_mu=True, seed=0)
+    eps = torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev)
+    mu = torch.from_numpy(p.mu.reshape(9, -1).copy()).to(dev)
+    P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, eps, mu)
+    del eps, mu
+    P.tune(vie.VIE_FP32)
+    P.tune(vie.VIE_FP64)
+    nr = p.nrhs
+    b = torch.empty((nr, 6, n, n, n), dtype=torch.complex128, device=dev)
+    P.rhs(p.directions, p.polarisations, nr, b)
+    J = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, info = P.solve(b, J, tol=1e-8, restart=30, max_outer=40, max_inner=1000, inner_tol=1e-5,
+                       mode=vie.VIE_SOLVE_MIXED, nrhs=nr, allow_noconv=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"workload": f"maxwell_mu_bump_{n}_x{nr}rhs", "nrhs": nr, "status": int(st), "seconds": dt,
+           "rhs_per_s": nr / dt, "rel_residual_max": info.rel_residual, "applies_fp32": info.applies_fp32,
+           "applies_fp64": info.applies_fp64, "gmres_iters_total": info.inner_iters,
+           "refinement_steps": info.outer_iters}
+    P.close()
+    return out
+
+
+def leg_maxwell256(args, dev):
+    """Maxwell with mu at 256^3 (10 wavelengths): mixed vs FP64 solve to 1e-8, one plane wave."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    n = 256
+    p = vi.maxwell_problem(n=n, wavelengths=10.0, with_mu=True, seed=0)
+    eps = torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev)
+    mu = torch.from_numpy(p.mu.reshape(9, -1).copy()).to(dev)
+    t0 = time.perf_counter()
+    P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, eps, mu)
+    t_setup = time.perf_counter() - t0
+    del eps, mu
+    P.tune(vie.VIE_FP32)
+    P.tune(vie.VIE_FP64)
+    b = torch.empty((6, n, n, n), dtype=torch.complex128, device=dev)
+    P.rhs(p.directions[0], p.polarisations[0], 1, b)
+    J = torch.zeros_like(b)
+    out = {"workload": f"maxwell_mu_bump_{n}", "setup_s": t_setup}
+    for name, mode in (("mixed", vie.VIE_SOLVE_MIXED), ("fp64", vie.VIE_SOLVE_FP64)):
+        J.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = P.solve(b, J, tol=1e-8, restart=50, max_outer=40, max_inner=600, inner_tol=1e-5, mode=mode,
+                           allow_noconv=True)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "status": int(st), "rel_residual": info.rel_residual,
+                     "applies_fp32": info.applies_fp32, "applies_fp64": info.applies_fp64,
+                     "gmres_iters": info.inner_iters}
+    out["speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    P.close()
+    return out
+
+
+def leg_serve(args, dev):
+    """Continuous-batching request mix: Poisson arrivals, n in {32..192}, 1-8 wavelengths,
+    Helmholtz / Maxwell (mu = I), 160 GB HBM budget; p50/p99 latency and solves/s."""
+    from paper_1805_04791_gb300 import serve
+    import vie_inputs as vi
+
+    reqs = vi.serving_mix(args.serve_requests, rate_per_s=args.serve_rate, seed=0)
+    srv = serve.Server(budget_bytes=160e9, max_slots=32, restart=30, tol=1e-8)
+    stats = srv.run(reqs)
+    out = stats.summary()
+    fails = {}
+    for r in stats.results:
+        if r.status != "ok":
+            fails[r.status[:160]] = fails.get(r.status[:160], 0) + 1
+    by_n = {}
+    for r in stats.results:
+        if r.status == "ok":
+            by_n.setdefault(r.n, []).append(r.latency_s)
+    out["failures"] = fails
+    out["p50_latency_by_n"] = {str(k): sorted(v)[len(v) // 2] for k, v in sorted(by_n.items())}
+    out.update({"rate_per_s": args.serve_rate, "budget_GB": 160, "tol": 1e-8,
+                "max_rel_residual": max((r.rel_residual for r in stats.results if r.status == "ok"), default=None)})
+    return out
 
 
 def run_ours(args):
@@ -378,6 +481,17 @@ def run_ours(args):
                for k in range(5)}
     apply_bytes = sum(abytes)
 
+    extra = {}
+    for leg in [x for x in args.legs.split(",") if x]:
+        t0 = time.perf_counter()
+        fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve}[leg]
+        try:
+            extra[leg] = fn(args, dev)
+        except Exception as e:  # report, do not lose the main line
+            extra[leg] = {"error": str(e)}
+        extra[leg]["leg_wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(n, reps=5)
@@ -406,6 +520,7 @@ def run_ours(args):
             "solve": solve, "setup_s": t_setup, "wall_s_timed": t_wall,
             "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk, "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     P.close()
     if world > 1:

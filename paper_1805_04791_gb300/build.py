@@ -21,7 +21,8 @@ LIB = os.path.join(LIBDIR, "libvie_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-SOURCES = ["capi.cu", "precompute.cu", "apply.cu", "krylov.cu"]
+SOURCES = ["capi.cu", "precompute.cu", "apply.cu", "krylov.cu"] + [
+    f"apply_fast_{m:03d}.cu" for m in (64, 96, 128, 192, 256, 384, 512)]
 
 
 def nvcc() -> str:
@@ -61,7 +62,7 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
             print(r.stderr, file=sys.stderr)
         return o
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     if force or not _newer(LIB, objs):
         cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs]

@@ -170,6 +170,8 @@ vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, in
     set_error("vie_eval_scattered: bad argument");
     return VIE_EINVAL;
   }
+  vie_status s = build_eval_kernels(P, (cudaStream_t)stream);
+  if (s != VIE_OK) return s;
   return run_apply(P, P->keval, J, field_out, VIE_FP64, nrhs, false, (cudaStream_t)stream);
 }
 

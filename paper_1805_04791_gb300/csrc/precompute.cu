@@ -228,7 +228,7 @@ template <int S>
 static vie_status fft_cube(double2* data, int M, const FftPlan& pl, const double2* tw, cudaStream_t st) {
   const int nl = pick_nl(M);
   const size_t smem = sizeof(double2) * (M + 2 * nl * (M + 1));
-  VIE_CK(cudaFuncSetAttribute(k_fft_cube<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VIE_CK(allow_smem(k_fft_cube<S>));
   dim3 blk(std::max(1, std::min(32, M / 16)), 1);
   blk.y = 256 / blk.x;
   for (int axis = 0; axis < 3; ++axis) {
@@ -307,7 +307,11 @@ static vie_status combine(vie_problem* P, KernelSet& K, int mode, const CombineD
   return VIE_OK;
 }
 
-vie_status build_kernels(vie_problem* P, cudaStream_t st) {
+// Compute the raw octant kernels of the symbols in `mask` (bit = Sym) that are
+// not computed yet.
+static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st) {
+  mask &= ~P->sym_mask;
+  if (!mask) return VIE_OK;
   const int n = P->n, sn = 3 * n, M = 2 * n;
   const double dk = 2.0 * M_PI / (3.0 * P->D);
   const int jmax = 3 * (sn / 2) * (sn / 2);
@@ -315,10 +319,11 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
   double2* tab = nullptr;
   double2 *F = nullptr, *E = nullptr, *tw_sn = nullptr;
   float2* tw_sn32 = nullptr;
+  const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = (long long)(n + 1) * (n + 1) * (n + 1);
+  if (!P->sym_oct) VIE_CK(dalloc((void**)&P->sym_oct, sizeof(double2) * SYM_COUNT * O3, st));
   VIE_CK(dalloc((void**)&tab, sizeof(double2) * (jmax + 1), st));
   k_ghat_table<<<(jmax + 256) / 256, 256, 0, st>>>(tab, jmax, dk, w, P->L);
   VIE_CK(cudaGetLastError());
-  const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = (long long)(n + 1) * (n + 1) * (n + 1);
   VIE_CK(dalloc((void**)&F, sizeof(double2) * S3, st));
   VIE_CK(dalloc((void**)&E, sizeof(double2) * M3, st));
   vie_status s = make_twiddles(sn, &tw_sn, &tw_sn32, st);
@@ -328,11 +333,9 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
     set_error("bad oversampled grid size");
     return VIE_EINVAL;
   }
-  VIE_CK(dalloc((void**)&P->sym_oct, sizeof(double2) * SYM_COUNT * O3, st));
-  const bool need1 = P->kind == VIE_MAXWELL;
   const int gb = 152 * 16;
   for (int sym = 0; sym < SYM_COUNT; ++sym) {
-    if (sym == SYM_1 && !need1) continue;
+    if (!(mask & (1u << sym))) continue;
     k_build_F<<<gb, 256, 0, st>>>(F, tab, sn, sym, dk);
     VIE_CK(cudaGetLastError());
     s = fft_cube<+1>(F, sn, plsn, tw_sn, st);
@@ -349,7 +352,39 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
   dfree(tab, st);
   dfree(tw_sn, st);
   dfree(tw_sn32, st);
+  P->sym_mask |= mask;
+  return VIE_OK;
+}
 
+static const unsigned kQmask = (1u << SYM_XX) | (1u << SYM_YY) | (1u << SYM_ZZ) | (1u << SYM_XY) | (1u << SYM_XZ) |
+                               (1u << SYM_YZ);
+static const unsigned kDmask = (1u << SYM_DX) | (1u << SYM_DY) | (1u << SYM_DZ);
+
+// Kernel sets: `which` 0 = operator apply, 1 = scattered field.
+static vie_status combine_sets(vie_problem* P, int which, cudaStream_t st);
+
+vie_status build_kernels(vie_problem* P, cudaStream_t st) {
+  // the operator needs -k_a k_b (and, for Maxwell, 1 and i k_a); the scattered
+  // field of Laplace/Helmholtz needs i k_a and is built on first use
+  const unsigned mask = P->kind == VIE_MAXWELL ? (kQmask | kDmask | (1u << SYM_1)) : kQmask;
+  vie_status s = compute_symbols(P, mask, st);
+  if (s != VIE_OK) return s;
+  return combine_sets(P, 0, st);
+}
+
+vie_status build_eval_kernels(vie_problem* P, cudaStream_t st) {
+  if (P->keval.oct64) return VIE_OK;
+  const unsigned mask = P->kind == VIE_MAXWELL ? (kQmask | kDmask | (1u << SYM_1)) : kDmask;
+  vie_status s = compute_symbols(P, mask, st);
+  if (s != VIE_OK) return s;
+  return combine_sets(P, 1, st);
+}
+
+static vie_status combine_sets(vie_problem* P, int which, cudaStream_t st) {
+  const int n = P->n, M = 2 * n;
+  const long long M3 = (long long)M * M * M;
+  const double w = P->kind == VIE_LAPLACE ? 0.0 : P->omega;
+  vie_status s = VIE_OK;
   // Fold constants: apply kernels give u with y = x + H u; the 1/(2n)^3 of the
   // inverse DFT is folded in too.
   const double nrm = 1.0 / (double)M3;
@@ -373,16 +408,20 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
       ca.sym[a][0] = Q[a];
       ca.fac[a][0] = make_double2(sg * nrm, 0);
     }
-    s = combine(P, P->kapply, KM_SYM3, ca, sg * 0.5 * nrm, 0x7, st);
-    if (s != VIE_OK) return s;
+    if (which == 0) {
+      s = combine(P, P->kapply, KM_SYM3, ca, sg * 0.5 * nrm, 0x7, st);
+      if (s != VIE_OK) return s;
+    }
     // phi_sc = div V J
     ce.narr = 3;
     for (int a = 0; a < 3; ++a) {
       ce.sym[a][0] = Dd[a];
       ce.fac[a][0] = make_double2(nrm, 0);
     }
-    s = combine(P, P->keval, KM_DIV, ce, 0.0, 0, st);
-    if (s != VIE_OK) return s;
+    if (which == 1) {
+      s = combine(P, P->keval, KM_DIV, ce, 0.0, 0, st);
+      if (s != VIE_OK) return s;
+    }
   } else {
     // Maxwell (Eq. (eq:intM)): u_J = Q' J + P' x M, u_M = Q' M - P' x J with
     // Q' = -2 (K + I/2 + w^2 V), P'_a = -2 i w K_{i k_a}.
@@ -399,8 +438,10 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
       ca.sym[6 + a][0] = Dd[a];
       ca.fac[6 + a][0] = make_double2(0, -2.0 * w * nrm);
     }
-    s = combine(P, P->kapply, P->has_mu ? KM_MAXWELL6 : KM_SYM3, ca, -nrm, 0x7, st);
-    if (s != VIE_OK) return s;
+    if (which == 0) {
+      s = combine(P, P->kapply, P->has_mu ? KM_MAXWELL6 : KM_SYM3, ca, -nrm, 0x7, st);
+      if (s != VIE_OK) return s;
+    }
     // E_sc = Q'' J + P'' x M, H_sc = Q'' M - P'' x J; Q'' = K + w^2 V, P''_a = i w K_{i k_a}
     ce.narr = 9;
     for (int a = 0; a < 6; ++a) {
@@ -415,8 +456,10 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
       ce.sym[6 + a][0] = Dd[a];
       ce.fac[6 + a][0] = make_double2(0, w * nrm);
     }
-    s = combine(P, P->keval, P->has_mu ? KM_MAXWELL6 : KM_EMRED, ce, 0.0, 0, st);
-    if (s != VIE_OK) return s;
+    if (which == 1) {
+      s = combine(P, P->keval, P->has_mu ? KM_MAXWELL6 : KM_EMRED, ce, 0.0, 0, st);
+      if (s != VIE_OK) return s;
+    }
   }
   VIE_CK(cudaStreamSynchronize(st));
   return VIE_OK;

@@ -1,13 +1,13 @@
 // Register-resident two-step FFT of length M = R1 * R2 for lines that are
-// processed by T = R2 threads each (R1 is a multiple of R2).
+// processed by T = R2 threads each (thread t owns the k1 rows t + R2 j < R1).
 //
 //   forward  X[k1 + R1 k2] = sum_{n2} W_R2^{n2 k2} W_M^{n2 k1} sum_{n1} W_R1^{n1 k1} x[R2 n1 + n2]
 //   inverse  x[R2 n1 + n2] = sum_{k1} W_R1^{-n1 k1} W_M^{-n2 k1} sum_{k2} W_R2^{-n2 k2} X[k1 + R1 k2]
 //
 // Step 1 of the forward transform runs in thread n2 (an R1-point DFT on its
 // registers), the twiddled result goes through shared memory once, and step 2
-// runs R1/T R2-point DFTs per thread.  After the forward transform thread t
-// holds X[k1 + R1 k2] for k1 = t + T j (j < R1/T) and all k2 -- exactly the
+// runs ceil(R1/T) R2-point DFTs per thread.  After the forward transform thread
+// t holds X[k1 + R1 k2] for k1 = t + T j < R1 and all k2 -- exactly the
 // layout the inverse transform starts from, so a pointwise multiply in k-space
 // (the kernel mixing of the convolution) needs no data movement.
 // Pruning for zero padding: the forward input may be limited to its first
@@ -59,14 +59,82 @@ __device__ __forceinline__ double cos_pi16(int j) {
   return c[j & 31];
 }
 
-// a * W_R^{S j} with W_R = exp(2 pi i / R) (R divides 32)
+// cos(2 pi j / 24), j = 0..23
+__device__ __forceinline__ double cos_2pi24(int j) {
+  const double c[24] = {1.0,
+                        0.96592582628906828675,
+                        0.86602540378443864676,
+                        0.70710678118654752440,
+                        0.5,
+                        0.25881904510252076235,
+                        0.0,
+                        -0.25881904510252076235,
+                        -0.5,
+                        -0.70710678118654752440,
+                        -0.86602540378443864676,
+                        -0.96592582628906828675,
+                        -1.0,
+                        -0.96592582628906828675,
+                        -0.86602540378443864676,
+                        -0.70710678118654752440,
+                        -0.5,
+                        -0.25881904510252076235,
+                        0.0,
+                        0.25881904510252076235,
+                        0.5,
+                        0.70710678118654752440,
+                        0.86602540378443864676,
+                        0.96592582628906828675};
+  return c[((j % 24) + 24) % 24];
+}
+
+// a * W_R^{S j} with W_R = exp(2 pi i / R) (R divides 32 or 24)
 template <int R, int S, typename T>
 __device__ __forceinline__ typename CT<T>::V twc(typename CT<T>::V a, int j) {
-  const int q = (j * (32 / R)) & 31;  // angle pi q / 16
-  const T c = (T)cos_pi16(q);
-  const T s = (T)S * (T)cos_pi16(q + 24);  // sin(pi q/16) = cos(pi (q - 8)/16)
+  T c, s;
+  if constexpr (32 % R == 0) {
+    const int q = (j * (32 / R)) & 31;  // angle pi q / 16
+    c = (T)cos_pi16(q);
+    s = (T)S * (T)cos_pi16(q + 24);  // sin(pi q/16) = cos(pi (q - 8)/16)
+  } else {
+    static_assert(24 % R == 0, "twiddle table covers R | 32 and R | 24");
+    const int q = (j * (24 / R)) % 24;  // angle 2 pi q / 24
+    c = (T)cos_2pi24(q);
+    s = (T)S * (T)cos_2pi24(q + 18);  // sin(t) = cos(t - pi/2)
+  }
   return CT<T>::make(c * a.x - s * a.y, c * a.y + s * a.x);
 }
+
+// DFT of length P Q on registers by the same two-step split as the line FFT:
+// X[k1 + P k2] = sum_{n2} W_Q^{n2 k2} W_{PQ}^{n2 k1} sum_{n1} W_P^{n1 k1} x[Q n1 + n2].
+template <int P, int Q, int S, typename T>
+struct DftPQ {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    V y[Q][P];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) y[n2][n1] = u[Q * n1 + n2];
+      Dft<P, S, T>::run(y[n2]);
+#pragma unroll
+      for (int k1 = 1; k1 < P; ++k1)
+        if (n2 != 0) y[n2][k1] = twc<P * Q, S, T>(y[n2][k1], n2 * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      V z[Q];
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) z[n2] = y[n2][k1];
+      Dft<Q, S, T>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) u[k1 + P * k2] = z[k2];
+    }
+  }
+};
+template <int S, typename T> struct Dft<6, S, T> : DftPQ<2, 3, S, T> {};
+template <int S, typename T> struct Dft<12, S, T> : DftPQ<4, 3, S, T> {};
+template <int S, typename T> struct Dft<24, S, T> : DftPQ<8, 3, S, T> {};
 
 template <int S, typename T> struct Dft<32, S, T> {
   typedef typename CT<T>::V V;
@@ -129,8 +197,10 @@ template <typename T, int R1, int R2>
 struct Fft2 {
   typedef typename CT<T>::V V;
   static constexpr int M = R1 * R2;
-  static constexpr int NT = R2;          // threads per line
-  static constexpr int J = R1 / R2;      // k1 rows per thread
+  static constexpr int NT = R2;                 // threads per line
+  static constexpr int J = (R1 + R2 - 1) / R2;  // k1 rows per thread (k1 = t + R2 j < R1)
+  // Does thread t own row j?  Always true when R2 divides R1.
+  static __device__ __forceinline__ bool row(int t, int j) { return (R1 % R2 == 0) || (t + R2 * j < R1); }
   static constexpr int PF = R2 + 1;      // forward transpose row pitch
   static constexpr int PI = R1 + 1;      // inverse transpose row pitch
   static constexpr int LS0 = (R1 * PF > R2 * PI ? R1 * PF : R2 * PI);
@@ -152,6 +222,7 @@ struct Fft2 {
   static __device__ __forceinline__ void fwd2(V (*X)[R2], int t, const V* s) {
 #pragma unroll
     for (int j = 0; j < J; ++j) {
+      if (!row(t, j)) continue;
       const int k1 = t + R2 * j;
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) X[j][n2] = s[k1 * PF + n2];
@@ -162,6 +233,7 @@ struct Fft2 {
   static __device__ __forceinline__ void invA(V (*X)[R2], int t, V* s, const V* tw) {
 #pragma unroll
     for (int j = 0; j < J; ++j) {
+      if (!row(t, j)) continue;
       const int k1 = t + R2 * j;
       Dft<R2, +1, T>::run(X[j]);
 #pragma unroll

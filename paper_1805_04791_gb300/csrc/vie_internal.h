@@ -78,6 +78,7 @@ struct vie_problem {
   double2* Hm64 = nullptr;   // [6][n^3] H_mu (Maxwell with mu)
   float2* Hm32 = nullptr;
   double2* sym_oct = nullptr;  // [SYM_COUNT][(n+1)^3] raw symbol kernels DFT_{2n}, FP64
+  unsigned sym_mask = 0;       // symbols computed so far
   vie::KernelSet kapply;     // operator kernels (with I/2, 2H sign and 1/(2n)^3 folded in)
   vie::KernelSet keval;      // scattered-field kernels
   vie::Workspace ws;         // padded intermediates
@@ -105,6 +106,7 @@ vie_status cuda_fail(cudaError_t e, const char* what);
 // precompute.cu
 vie_status build_medium(vie_problem* P, const void* eps, const void* mu, cudaStream_t st);
 vie_status build_kernels(vie_problem* P, cudaStream_t st);
+vie_status build_eval_kernels(vie_problem* P, cudaStream_t st);
 vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st);
 
 // apply.cu
@@ -121,6 +123,25 @@ vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant
 vie_status run_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_opts* opt, vie_solve_info* info,
                      cudaStream_t st);
 vie_status run_rhs(vie_problem* P, const double* d, const double* p, int nrhs, void* out, cudaStream_t st);
+
+// Allow a kernel the device's full opt-in dynamic shared memory.  The attribute
+// is process-wide per kernel: setting it to each launch's own size would race
+// between threads launching the same kernel with different sizes (one lowers
+// the limit under the other's launch), so it is always set to the same maximum.
+inline int smem_optin_bytes() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    v = b > 0 ? b : 48 * 1024;
+  }
+  return v;
+}
+template <typename K>
+inline cudaError_t allow_smem(K* kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_bytes());
+}
 
 inline int cin_of(int mode) { return mode == KM_MAXWELL6 ? 6 : 3; }
 inline int cout_of(int mode) { return mode == KM_SYM3 ? 3 : (mode == KM_DIV ? 1 : 6); }

@@ -336,8 +336,9 @@ def test_fast_and_generic_paths_agree_with_oracle(vie, n, monkeypatch):
         assert rel(y, yo) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("kind,n,mu", [("helmholtz", 32, False), ("maxwell", 32, True), ("helmholtz", 64, False)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind,n,mu", [("helmholtz", 32, False), ("maxwell", 32, True), ("helmholtz", 64, False),
+                                       ("helmholtz", 48, False), ("maxwell", 48, True), ("laplace", 96, False)])
 def test_every_zpass_variant_matches_oracle(vie, monkeypatch, variant, kind, n, mu):
     """Each schedule the autotuner can pick (forced with VIE_P3_VARIANT) reproduces the oracle."""
     import torch
@@ -371,6 +372,6 @@ def test_tune_entry_point(vie):
     P2 = vie.Problem("helmholtz", 32, -1.0, 1.0, p.omega, eps_dev(vi.helmholtz_problem(n=32, wavelengths=4.0)))
     v32 = P2.tune(m.VIE_FP32)
     v64 = P2.tune(m.VIE_FP64)
-    assert 0 <= v32 < 5 and 0 <= v64 < 5
+    assert 0 <= v32 < 4 and 0 <= v64 < 4
     assert P.tune(m.VIE_FP32) == -1  # 2n = 48 uses the generic kernels
     P2.close()
