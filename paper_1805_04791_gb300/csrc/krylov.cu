@@ -93,7 +93,7 @@ vie_status run_rhs(vie_problem* P, const double* d, const double* p, int nrhs, v
 // one batched operator apply over the group and one batched reduction, with a
 // single device-to-host copy of all the group's Hessenberg columns.  Device
 // layout of a group: vectors [r][L] (r < nb); Krylov basis [i][r][L].
-static const int kRedBlocks = 304;  // 2 x 152 SMs
+static const int kRedBlocks = 608;  // 4 x 152 SMs
 static const int kRedThreads = 256;
 static const int kDotChunk = 8;
 
@@ -122,7 +122,22 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__
     AT ar[kDotChunk], ai[kDotChunk];
 #pragma unroll
     for (int t = 0; t < kDotChunk; ++t) ar[t] = ai[t] = (AT)0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)G * blockDim.x) {
+    const long long stride = (long long)G * blockDim.x;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // two elements per iteration: twice the loads in flight per thread
+    for (; e + stride < L; e += 2 * stride) {
+      const TB wa = wr[e], wb = wr[e + stride];
+#pragma unroll
+      for (int t = 0; t < kDotChunk; ++t)
+        if (t < cnt) {
+          const int i = i0 + t;
+          const TB va = (i < k) ? Vr[(long long)i * ldi + e] : wa;
+          const TB vb = (i < k) ? Vr[(long long)i * ldi + e + stride] : wb;
+          ar[t] += va.x * wa.x + va.y * wa.y + vb.x * wb.x + vb.y * wb.y;
+          ai[t] += va.x * wa.y - va.y * wa.x + vb.x * wb.y - vb.y * wb.x;
+        }
+    }
+    for (; e < L; e += stride) {
       const TB we = wr[e];
 #pragma unroll
       for (int t = 0; t < kDotChunk; ++t)
@@ -193,12 +208,25 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(TB* __restrict__ w, c
   AT nn = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
     TB acc = wr[e];
-    for (int i = 0; i < k; ++i) {
+    AT sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const TB v = Vr[(long long)(i + u) * ldi + e];
+        const typename Acc<TB>::V c = cs[i + u];
+        sx[u] += c.x * v.x - c.y * v.y;
+        sy[u] += c.x * v.y + c.y * v.x;
+      }
+    }
+    for (; i < k; ++i) {
       const TB v = Vr[(long long)i * ldi + e];
       const typename Acc<TB>::V c = cs[i];
-      acc.x -= c.x * v.x - c.y * v.y;
-      acc.y -= c.x * v.y + c.y * v.x;
+      sx[0] += c.x * v.x - c.y * v.y;
+      sy[0] += c.x * v.y + c.y * v.x;
     }
+    acc.x -= (sx[0] + sx[1]) + (sx[2] + sx[3]);
+    acc.y -= (sy[0] + sy[1]) + (sy[2] + sy[3]);
     wr[e] = acc;
     nn += acc.x * acc.x + acc.y * acc.y;
   }
@@ -239,17 +267,31 @@ __global__ void k_update(double2* __restrict__ x, const TB* __restrict__ V, long
   }
 }
 
-// dst[r] = scale[r] * src[r] (types may differ).  grid = (blocks, nb).
+// dst[r] = scale[r] * src[r].  grid = (blocks, nb).  FP32 -> FP32 scales in
+// FP32 (FP64 conversions run on GB300's slow FP64 pipe); FP64 -> FP32 rounds
+// the FP64 product once.
 template <typename TD, typename TS>
 __global__ void k_scale(TD* __restrict__ dst, const TS* __restrict__ src, const double* __restrict__ scale,
                         long long L) {
   const int r = blockIdx.y;
-  const double sc = scale[r];
   TD* d = dst + (long long)r * L;
   const TS* s = src + (long long)r * L;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
-    d[e].x = sc * (double)s[e].x;
-    d[e].y = sc * (double)s[e].y;
+  if constexpr (sizeof(TD) == sizeof(float2) && sizeof(TS) == sizeof(float2)) {
+    const float sc = (float)scale[r];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L;
+         e += (long long)gridDim.x * blockDim.x) {
+      const TS v = s[e];
+      d[e].x = sc * v.x;
+      d[e].y = sc * v.y;
+    }
+  } else {
+    const double sc = scale[r];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L;
+         e += (long long)gridDim.x * blockDim.x) {
+      const TS v = s[e];
+      d[e].x = sc * (double)v.x;
+      d[e].y = sc * (double)v.y;
+    }
   }
 }
 
@@ -259,7 +301,7 @@ __global__ void k_bminus(double2* __restrict__ r, const double2* __restrict__ b,
     r[e] = b[e] - r[e];
 }
 
-static int ew_blocks(long long L) { return (int)std::min<long long>((L + 255) / 256, 152LL * 8); }
+static int ew_blocks(long long L) { return (int)std::min<long long>((L + 255) / 256, 152LL * 16); }
 
 struct Group {
   int nb = 1;
