@@ -28,6 +28,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -62,10 +64,12 @@ def parse():
     ap.add_argument("--solves", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
-    ap.add_argument("--legs", default="",
+    ap.add_argument("--legs", default="laplace32,maxwell256,batched,serve",
                     help="comma list of extra legs: batched (Maxwell 128^3 with mu, 64 plane waves, lockstep "
                          "GMRES), maxwell256 (Maxwell 256^3 with mu: mixed vs FP64 time to 1e-8), serve "
-                         "(continuous-batching request mix)")
+                         "(continuous-batching request mix), paper (Bi-CGStab matvec counts on the paper's "
+                         "media beside Tables 2-5), laplace32 (electrostatic 32^3 FP64 solve to 1e-10)")
+    ap.add_argument("--paper-n", type=int, default=70)
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--batched-rhs", type=int, default=64)
@@ -323,6 +327,82 @@ def leg_serve(args, dev):
     return out
 
 
+def leg_paper(args, dev):
+    """Bi-CGStab (the paper's solver) on the paper's four media (Sec. 5.2, [0,1]^3,
+    E_in = (0, 0, exp(i w x))) at n = --paper-n, FP64, tolerance 1e-12; matvec counts
+    for the Helmholtz and reduced Maxwell equations beside the printed Tables 2-5."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as f:
+        table = json.load(f)["rows"]
+    n = args.paper_n
+    d = np.array([1.0, 0.0, 0.0])
+    pol = np.array([0.0, 0.0, 1.0])
+    out = {"n": n, "tol": 1e-12, "rows": []}
+    for medium in ("eps222", "eps234", "eps_dense", "eps444"):
+        eps = torch.from_numpy(vi.paper_medium(medium, n, 0.0, 1.0).reshape(9, -1).copy()).to(dev)
+        for size in (1e-10, 1.0, 5.0):
+            printed = [r["N_matvec"] for r in table if r["medium"] == medium and r["size_wavelengths"] == size]
+            row = {"medium": medium, "size": size, "paper_N_matvec": printed}
+            for kind in ("helmholtz", "maxwell"):
+                P = vie.Problem(kind, n, 0.0, 1.0, 2 * np.pi * size, eps)
+                b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
+                P.rhs(d, pol if kind == "maxwell" else None, 1, b)
+                J = torch.zeros_like(b)
+                t0 = time.perf_counter()
+                st, info = P.solve(b, J, tol=1e-12, max_inner=4000, mode=vie.VIE_SOLVE_BICGSTAB, allow_noconv=True)
+                torch.cuda.synchronize()
+                row[kind] = {"N_matvec": info.applies_fp64, "seconds": time.perf_counter() - t0,
+                             "rel_residual": info.rel_residual, "status": int(st)}
+                P.close()
+            out["rows"].append(row)
+        del eps
+    return out
+
+
+def leg_laplace32(args, dev):
+    """Electrostatic workload: anisotropic Laplace bump, 32^3 on [-1,1]^3, uniform E0 = z,
+    FP64 GMRES to 1e-10 (time to solution over repeated solves)."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    p = vi.laplace_bump_problem(n=32, seed=0)
+    P = vie.Problem("laplace", 32, p.lo, p.hi, 0.0, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev))
+    P.tune(vie.VIE_FP64)
+    b = torch.empty((3, 32, 32, 32), dtype=torch.complex128, device=dev)
+    P.rhs(p.directions[0], None, 1, b)
+    J = torch.zeros_like(b)
+    ts = []
+    for r in range(11):
+        J.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = P.solve(b, J, tol=1e-10, restart=50, mode=vie.VIE_SOLVE_FP64)
+        torch.cuda.synchronize()
+        if r:
+            ts.append(time.perf_counter() - t0)
+    x = torch.randn((3, 32, 32, 32), dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(5):
+        P.apply(x, y, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(200):
+        P.apply(x, y, vie.VIE_FP64)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"p50_s": pct(ts, 50), "p99_s": pct(ts, 99), "gmres_iters": info.inner_iters,
+           "rel_residual": info.rel_residual, "fp64_apply_us": 1000 * e0.elapsed_time(e1) / 200}
+    P.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -484,7 +564,8 @@ def run_ours(args):
     extra = {}
     for leg in [x for x in args.legs.split(",") if x]:
         t0 = time.perf_counter()
-        fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve}[leg]
+        fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve, "paper": leg_paper,
+              "laplace32": leg_laplace32}[leg]
         try:
             extra[leg] = fn(args, dev)
         except Exception as e:  # report, do not lose the main line

@@ -65,9 +65,11 @@ typedef enum { VIE_LAPLACE = 0, VIE_HELMHOLTZ = 1, VIE_MAXWELL = 2 } vie_kind;
  * iterations of the mixed-precision solve). */
 typedef enum { VIE_FP64 = 0, VIE_FP32 = 1 } vie_precision;
 
-/* Solver modes for vie_solve: plain FP64 GMRES(m), or FP32-inner GMRES(m)
- * inside an FP64 iterative-refinement loop. */
-typedef enum { VIE_SOLVE_FP64 = 0, VIE_SOLVE_MIXED = 1 } vie_solve_mode;
+/* Solver modes for vie_solve: plain FP64 GMRES(m); FP32-inner GMRES(m)
+ * inside an FP64 iterative-refinement loop; or FP64 Bi-CGStab, the solver of
+ * the paper's experiments (Sec. 5; restart and inner_tol unused, max_inner =
+ * iteration limit, two applies per iteration). */
+typedef enum { VIE_SOLVE_FP64 = 0, VIE_SOLVE_MIXED = 1, VIE_SOLVE_BICGSTAB = 2 } vie_solve_mode;
 
 typedef struct vie_problem vie_problem;
 
@@ -93,7 +95,9 @@ typedef struct {
 /* Create a problem: grid, medium and frequency (Sec. 2 / Eq. (Laplace_Scalar),
  * Sec. 3 / Eq. (Helmholtz0), Sec. 4 / Eq. (Maxwell)).
  *   kind   vie_kind.
- *   n      points per axis, n = 2^a 3^b with 4 <= n <= 256.
+ *   n      points per axis, n = 2^a 3^b 5^c 7^d 11^e with 4 <= n <= 256 (register-
+ *          resident kernels for 2n in {64, 96, 128, 192, 256, 384, 512}, shared-
+ *          memory Stockham kernels for the other sizes).
  *   lo, hi box [lo, hi]^3 (hi > lo).
  *   omega  angular frequency (ignored for Laplace; >= 0).
  *   eps    device, FP64 complex [9][n][n][n], the 3x3 tensor row-major per node;

@@ -27,10 +27,11 @@ vie_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_ECUDA;
 }
 
+// Grid sizes whose 2n and 3n transforms factor into the codelet radices.
 static bool smooth_size(int n) {
   if (n < 4 || n > 256) return false;
-  while (n % 2 == 0) n /= 2;
-  while (n % 3 == 0) n /= 3;
+  for (int p : {2, 3, 5, 7, 11})
+    while (n % p == 0) n /= p;
   return n == 1;
 }
 
@@ -74,7 +75,7 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
     return VIE_EINVAL;
   }
   if (!smooth_size(n)) {
-    set_error("n must be 2^a 3^b with 4 <= n <= 256");
+    set_error("n must be 2^a 3^b 5^c 7^d 11^e with 4 <= n <= 256");
     return VIE_EINVAL;
   }
   if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi)) {
@@ -158,7 +159,7 @@ vie_status vie_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_o
   if (!P || !rhs || !J || !opt || opt->nrhs < 1 || opt->restart < 1 || opt->restart > 200 || !(opt->tol > 0) ||
       opt->max_inner < 1 || opt->max_outer < 0 ||
       (opt->mode == VIE_SOLVE_MIXED && !(opt->inner_tol > 0 && opt->inner_tol < 1)) ||
-      (opt->mode != VIE_SOLVE_FP64 && opt->mode != VIE_SOLVE_MIXED)) {
+      (opt->mode != VIE_SOLVE_FP64 && opt->mode != VIE_SOLVE_MIXED && opt->mode != VIE_SOLVE_BICGSTAB)) {
     set_error("vie_solve: bad argument");
     return VIE_EINVAL;
   }

@@ -3,6 +3,7 @@
 // Sec. 1 and Sec. 6 name GMRES (and Bi-CGStab, used in Sec. 5) as the
 // iterative solvers for these second-kind equations.  Two modes:
 //  * FP64: restarted GMRES(m) on the FP64 apply, FP64 everywhere.
+//  * Bi-CGStab (the solver of Sec. 5) on the FP64 apply.
 //  * mixed: FP64 iterative refinement r = b - A x (FP64 apply), inner GMRES(m)
 //    on the FP32 apply with an FP32 Krylov basis; Hessenberg matrix, Givens
 //    rotations, least squares and the iterate x in FP64.
@@ -526,6 +527,177 @@ static int pick_group(vie_problem* P, int nrhs, int m, bool mixed) {
   return (int)std::max<long long>(1, std::min<long long>(nb, std::min(nrhs, 64)));
 }
 
+// ------------------------------------------------------------ Bi-CGStab
+// Unpreconditioned Bi-CGStab (van der Vorst 1992), the solver the paper's
+// experiments use (Sec. 5), on the FP64 apply; two operator applies per
+// iteration.  Reductions: up to four inner products conj(a_i) b_i per pass.
+struct Dots4 {
+  const double2* a[4];
+  const double2* b[4];
+  int k;
+};
+
+__global__ void __launch_bounds__(kRedThreads) k_dots4(Dots4 d, long long L, double2* partial) {
+  __shared__ double2 red[kRedThreads / 32][4];
+  double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < d.k) {
+        const double2 x = d.a[t][e], y = d.b[t][e];
+        ar[t] += x.x * y.x + x.y * y.y;
+        ai[t] += x.x * y.y - x.y * y.x;
+      }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    double2 a = make_double2(ar[t], ai[t]);
+    for (int off = 16; off > 0; off >>= 1) {
+      a.x += __shfl_down_sync(0xffffffffu, a.x, off);
+      a.y += __shfl_down_sync(0xffffffffu, a.y, off);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < d.k) {
+    double2 sm = make_double2(0, 0);
+    for (int w = 0; w < kRedThreads / 32; ++w) sm = sm + red[w][threadIdx.x];
+    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = sm;
+  }
+}
+
+// y = a0 x0 + a1 x1 + a2 x2 (x_i may be null; y may alias x0)
+__global__ void k_lincomb(double2* y, const double2* x0, double2 a0, const double2* x1, double2 a1, const double2* x2,
+                          double2 a2, long long L) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
+    double2 v = make_double2(0, 0);
+    if (x0) v = v + cmul(a0, x0[e]);
+    if (x1) v = v + cmul(a1, x1[e]);
+    if (x2) v = v + cmul(a2, x2[e]);
+    y[e] = v;
+  }
+}
+
+static vie_status dots_host(Dots4 d, long long L, double2* partial, double2* dev, std::vector<cd>& out,
+                            cudaStream_t st) {
+  k_dots4<<<kRedBlocks, kRedThreads, 0, st>>>(d, L, partial);
+  VIE_CK(cudaGetLastError());
+  k_reduce_partials<<<dim3(d.k, 1), 256, 0, st>>>(partial, d.k, kRedBlocks, 0, dev, 0);
+  VIE_CK(cudaGetLastError());
+  double2 h[4];
+  VIE_CK(cudaMemcpyAsync(h, dev, sizeof(double2) * d.k, cudaMemcpyDeviceToHost, st));
+  VIE_CK(cudaStreamSynchronize(st));
+  out.resize(d.k);
+  for (int i = 0; i < d.k; ++i) out[i] = cd(h[i].x, h[i].y);
+  return VIE_OK;
+}
+
+static vie_status run_bicgstab(vie_problem* P, const void* rhs, void* Jv, const vie_solve_opts* opt,
+                               vie_solve_info* inf, double* worst, bool* all_conv, cudaStream_t st) {
+  const long long L = (long long)P->ncomp * P->n * P->n * P->n;
+  const size_t need = sizeof(double2) * (6 * L + (size_t)4 * kRedBlocks + 8) + 8 * 256;
+  if (P->ks.bytes < need) {
+    dfree(P->ks.buf, st);
+    P->ks.buf = nullptr;
+    P->ks.bytes = 0;
+    if (dalloc(&P->ks.buf, need, st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("out of device memory for the Bi-CGStab vectors");
+      return VIE_ENOMEM;
+    }
+    P->ks.bytes = need;
+  }
+  double2* base = (double2*)P->ks.buf;
+  double2 *r = base, *rh = base + L, *p = base + 2 * L, *v = base + 3 * L, *sv = base + 4 * L, *tv = base + 5 * L;
+  double2* partial = base + 6 * L;
+  double2* dev = partial + 4 * kRedBlocks;
+  const int eb = ew_blocks(L);
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  auto C = [](cd z) { return make_double2(z.real(), z.imag()); };
+  *all_conv = true;
+  for (int rr = 0; rr < opt->nrhs; ++rr) {
+    const double2* b = (const double2*)rhs + rr * L;
+    double2* x = (double2*)Jv + rr * L;
+    std::vector<cd> d;
+    Dots4 q{{b, x, nullptr, nullptr}, {b, x, nullptr, nullptr}, 2};
+    vie_status s = dots_host(q, L, partial, dev, d, st);
+    if (s != VIE_OK) return s;
+    const double nb = std::sqrt(std::max(0.0, d[0].real())), nx = std::sqrt(std::max(0.0, d[1].real()));
+    if (!std::isfinite(nb)) {
+      set_error("non-finite right-hand side");
+      return VIE_ENAN;
+    }
+    if (nb == 0.0) {
+      VIE_CK(cudaMemsetAsync(x, 0, sizeof(double2) * L, st));
+      continue;
+    }
+    if (nx == 0.0) {
+      VIE_CK(cudaMemcpyAsync(r, b, sizeof(double2) * L, cudaMemcpyDeviceToDevice, st));
+    } else {
+      s = run_apply(P, P->kapply, x, r, VIE_FP64, 1, true, st);
+      if (s != VIE_OK) return s;
+      ++inf->applies_fp64;
+      k_bminus<<<eb, 256, 0, st>>>(r, b, L);
+    }
+    VIE_CK(cudaMemcpyAsync(rh, r, sizeof(double2) * L, cudaMemcpyDeviceToDevice, st));
+    VIE_CK(cudaMemsetAsync(p, 0, sizeof(double2) * L, st));
+    VIE_CK(cudaMemsetAsync(v, 0, sizeof(double2) * L, st));
+    cd rho = 1, alpha = 1, omega = 1;
+    double rel = 1.0;
+    bool conv = false;
+    for (int it = 0; it < opt->max_inner; ++it) {
+      q = Dots4{{rh, r, nullptr, nullptr}, {r, r, nullptr, nullptr}, 2};
+      s = dots_host(q, L, partial, dev, d, st);
+      if (s != VIE_OK) return s;
+      rel = std::sqrt(std::max(0.0, d[1].real())) / nb;
+      if (!std::isfinite(rel)) {
+        set_error("non-finite residual");
+        return VIE_ENAN;
+      }
+      if (rel <= opt->tol) {
+        conv = true;
+        break;
+      }
+      const cd rho_new = d[0];
+      const cd beta = (rho_new / rho) * (alpha / omega);
+      rho = rho_new;
+      // p = r + beta (p - omega v)
+      k_lincomb<<<eb, 256, 0, st>>>(p, r, one, p, C(beta), v, C(-beta * omega), L);
+      s = run_apply(P, P->kapply, p, v, VIE_FP64, 1, true, st);
+      if (s != VIE_OK) return s;
+      ++inf->applies_fp64;
+      q = Dots4{{rh, nullptr, nullptr, nullptr}, {v, nullptr, nullptr, nullptr}, 1};
+      s = dots_host(q, L, partial, dev, d, st);
+      if (s != VIE_OK) return s;
+      alpha = rho / d[0];
+      k_lincomb<<<eb, 256, 0, st>>>(sv, r, one, v, C(-alpha), nullptr, zero, L);
+      q = Dots4{{sv, nullptr, nullptr, nullptr}, {sv, nullptr, nullptr, nullptr}, 1};
+      s = dots_host(q, L, partial, dev, d, st);
+      if (s != VIE_OK) return s;
+      if (std::sqrt(std::max(0.0, d[0].real())) / nb <= opt->tol) {
+        k_lincomb<<<eb, 256, 0, st>>>(x, x, one, p, C(alpha), nullptr, zero, L);
+        rel = std::sqrt(std::max(0.0, d[0].real())) / nb;
+        conv = true;
+        ++inf->inner_iters;
+        break;
+      }
+      s = run_apply(P, P->kapply, sv, tv, VIE_FP64, 1, true, st);
+      if (s != VIE_OK) return s;
+      ++inf->applies_fp64;
+      q = Dots4{{tv, tv, nullptr, nullptr}, {sv, tv, nullptr, nullptr}, 2};
+      s = dots_host(q, L, partial, dev, d, st);
+      if (s != VIE_OK) return s;
+      omega = d[0] / d[1];
+      k_lincomb<<<eb, 256, 0, st>>>(x, x, one, p, C(alpha), sv, C(omega), L);
+      k_lincomb<<<eb, 256, 0, st>>>(r, sv, one, tv, C(-omega), nullptr, zero, L);
+      VIE_CK(cudaGetLastError());
+      ++inf->inner_iters;
+    }
+    *worst = std::max(*worst, rel);
+    if (!conv) *all_conv = false;
+  }
+  return VIE_OK;
+}
+
 vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_opts* opt, vie_solve_info* info,
                      cudaStream_t st) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -535,6 +707,20 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
   vie_solve_info inf{};
   vie_status final_status = VIE_OK;
   double worst = 0.0;
+  if (opt->mode == VIE_SOLVE_BICGSTAB) {
+    bool all = true;
+    vie_status s = run_bicgstab(P, rhs, Jv, opt, &inf, &worst, &all, st);
+    if (s != VIE_OK) return s;
+    VIE_CK(cudaStreamSynchronize(st));
+    inf.rel_residual = worst;
+    inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    if (!all) {
+      set_error("Bi-CGStab did not reach the tolerance within max_inner iterations");
+      return VIE_ENOCONV;
+    }
+    return VIE_OK;
+  }
   const int gsz = pick_group(P, opt->nrhs, m, mixed);
   for (int r0 = 0; r0 < opt->nrhs; r0 += gsz) {
     const int nb = std::min(gsz, opt->nrhs - r0);

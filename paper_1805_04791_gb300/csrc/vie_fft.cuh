@@ -1,7 +1,7 @@
 // Device-side building blocks shared by every kernel of the library:
 // complex arithmetic on CUDA vector types, small DFT codelets, and a
-// shared-memory mixed-radix (2, 3, 4, 8, 16) Stockham FFT that transforms a
-// tile of lines resident in shared memory.
+// shared-memory mixed-radix (2, 3, 4, 5, 7, 8, 11, 16) Stockham FFT that
+// transforms a tile of lines resident in shared memory.
 //
 // The FFT is the engine of the truncated-kernel method of Sec. 5 (steps a-c:
 // truncate the Green's function, transform it, cut off at the grid Nyquist
@@ -190,6 +190,82 @@ template <int S, typename T> struct Dft<16, S, T> {
   }
 };
 
+// Odd prime R in {5, 7, 11}: with H = (R - 1)/2 and q = 1..H,
+//   A_q = u_0 + sum_{r=1}^{H} (u_r + u_{R-r}) cos(2 pi r q / R)
+//   B_q =       sum_{r=1}^{H} (u_r - u_{R-r}) sin(2 pi r q / R)
+//   U_q = A_q + S i B_q,  U_{R-q} = A_q - S i B_q,  U_0 = sum_r u_r.
+template <int R> struct OddRoots;
+template <> struct OddRoots<5> {
+  static __device__ __forceinline__ double c(int j) {
+    const double t[3] = {1.0, 0.309016994374947424102, -0.809016994374947424102};
+    return t[j];
+  }
+  static __device__ __forceinline__ double s(int j) {
+    const double t[3] = {0.0, 0.951056516295153572116, 0.587785252292473129169};
+    return t[j];
+  }
+};
+template <> struct OddRoots<7> {
+  static __device__ __forceinline__ double c(int j) {
+    const double t[4] = {1.0, 0.623489801858733530525, -0.222520933956314404289, -0.900968867902419126236};
+    return t[j];
+  }
+  static __device__ __forceinline__ double s(int j) {
+    const double t[4] = {0.0, 0.781831482468029808708, 0.974927912181823607018, 0.433883739117558120476};
+    return t[j];
+  }
+};
+template <> struct OddRoots<11> {
+  static __device__ __forceinline__ double c(int j) {
+    const double t[6] = {1.0, 0.841253532831181168862, 0.415415013001886425529, -0.142314838273285140444,
+                         -0.654860733945285064057, -0.95949297361449738989};
+    return t[j];
+  }
+  static __device__ __forceinline__ double s(int j) {
+    const double t[6] = {0.0, 0.540640817455597582108, 0.909631995354518371412, 0.989821441880932732376,
+                         0.755749574354258283774, 0.281732556841429697711};
+    return t[j];
+  }
+};
+
+template <int R, int S, typename T>
+struct DftOdd {
+  typedef typename CT<T>::V V;
+  static __device__ __forceinline__ void run(V* u) {
+    constexpr int H = (R - 1) / 2;
+    V a[H + 1], b[H + 1];
+    V sum = u[0];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      a[r] = u[r] + u[R - r];
+      b[r] = u[r] - u[R - r];
+      sum = sum + a[r];
+    }
+    const V u0 = u[0];
+    u[0] = sum;
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      T ax = u0.x, ay = u0.y, bx = 0, by = 0;
+#pragma unroll
+      for (int r = 1; r <= H; ++r) {
+        int j = (r * q) % R;
+        const T cs = (T)OddRoots<R>::c(j <= H ? j : R - j);
+        const T sn = (j <= H) ? (T)OddRoots<R>::s(j) : -(T)OddRoots<R>::s(R - j);
+        ax += cs * a[r].x;
+        ay += cs * a[r].y;
+        bx += sn * b[r].x;
+        by += sn * b[r].y;
+      }
+      // S i B = (-S by, S bx)
+      u[q] = CT<T>::make(ax - (T)S * by, ay + (T)S * bx);
+      u[R - q] = CT<T>::make(ax + (T)S * by, ay - (T)S * bx);
+    }
+  }
+};
+template <int S, typename T> struct Dft<5, S, T> : DftOdd<5, S, T> {};
+template <int S, typename T> struct Dft<7, S, T> : DftOdd<7, S, T> {};
+template <int S, typename T> struct Dft<11, S, T> : DftOdd<11, S, T> {};
+
 // ------------------------------------------------------------ FFT plan
 struct FftPlan {
   int M;      // transform length
@@ -197,23 +273,19 @@ struct FftPlan {
   int R[8];   // radices, first stage first
 };
 
-// Factor M = 2^a 3^b into radices 16, 8, 4, 2 and 3; returns false if M has other factors.
+// Factor M = 2^a 3^b 5^c 7^d 11^e into radices 16, 8, 4, 2, 3, 5, 7, 11;
+// returns false if M has other factors.
 inline bool make_plan(int M, FftPlan* pl) {
   pl->M = M;
   pl->ns = 0;
   int m = M;
-  const int rad[4] = {16, 8, 4, 2};
-  for (int k = 0; k < 4; ++k)
+  const int rad[8] = {16, 8, 4, 2, 3, 5, 7, 11};
+  for (int k = 0; k < 8; ++k)
     while (m % rad[k] == 0 && m > 1) {
       if (pl->ns >= 8) return false;
       pl->R[pl->ns++] = rad[k];
       m /= rad[k];
     }
-  while (m % 3 == 0) {
-    if (pl->ns >= 8) return false;
-    pl->R[pl->ns++] = 3;
-    m /= 3;
-  }
   return m == 1 && M >= 2;
 }
 
@@ -265,7 +337,10 @@ __device__ typename CT<T>::V* tile_fft(typename CT<T>::V* a, typename CT<T>::V* 
       case 8: stage<8, S, T>(a, b, pl.M, p, tw, nl, ls); break;
       case 4: stage<4, S, T>(a, b, pl.M, p, tw, nl, ls); break;
       case 2: stage<2, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      default: stage<3, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 3: stage<3, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 5: stage<5, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 7: stage<7, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      default: stage<11, S, T>(a, b, pl.M, p, tw, nl, ls); break;
     }
     __syncthreads();
     typename CT<T>::V* t = a;

@@ -184,7 +184,7 @@ def test_invalid_arguments(vie):
 
     p = vi.laplace_bump_problem(n=8)
     e = eps_dev(p)
-    for bad in [dict(n=5), dict(n=7), dict(n=512), dict(lo=1.0, hi=1.0), dict(omega=-1.0)]:
+    for bad in [dict(n=3), dict(n=13), dict(n=26), dict(n=512), dict(lo=1.0, hi=1.0), dict(omega=-1.0)]:
         kw = dict(kind=vie.VIE_LAPLACE, n=8, lo=-1.0, hi=1.0, omega=0.0)
         kw.update(bad)
         with pytest.raises(vie.VieError) as ei:
@@ -375,3 +375,46 @@ def test_tune_entry_point(vie):
     assert 0 <= v32 < 4 and 0 <= v64 < 4
     assert P.tune(m.VIE_FP32) == -1  # 2n = 48 uses the generic kernels
     P2.close()
+
+
+@pytest.mark.parametrize("kind,n", [("laplace", 10), ("helmholtz", 14), ("helmholtz", 20), ("maxwell", 22),
+                                    ("helmholtz", 50)])
+def test_radix_5_7_11_sizes(vie, kind, n):
+    """Grid sizes with factors 5, 7, 11 (the paper's n = 50, 70, ..., 220 need them)."""
+    import torch
+
+    p = make_problem(kind, n, 2.0, False, seed=3)
+    P = vie.Problem(kind, n, p.lo, p.hi, p.omega, eps_dev(p), mu_dev(p))
+    op = operators.OracleProblem.from_problem(p)
+    x = vi.random_field(n, op.ncomp, 12)[0]
+    for prec, dt, tol in ((vie.VIE_FP64, torch.complex128, 1e-12), (vie.VIE_FP32, torch.complex64, 2e-5)):
+        xd = to_dev(x, dt)
+        yd = torch.empty_like(xd)
+        P.apply(xd, yd, prec)
+        torch.cuda.synchronize()
+        ref = op.apply(x if prec == vie.VIE_FP64 else x.astype(np.complex64).astype(np.complex128))
+        assert rel(yd.cpu().numpy(), ref) <= tol
+    P.close()
+
+
+@pytest.mark.parametrize("medium,kind", [("eps234", "helmholtz"), ("eps_dense", "maxwell")])
+def test_bicgstab_matches_oracle_on_paper_media(vie, medium, kind):
+    """The paper's solver (Sec. 5) on its media (Sec. 5.2): same solution and matvec count as the oracle."""
+    import torch
+
+    n, size = 20, 1.0
+    eps = vi.paper_medium(medium, n, 0.0, 1.0)
+    omega = 2 * math.pi * size
+    P = vie.Problem(kind, n, 0.0, 1.0, omega, to_dev(eps.reshape(9, -1)))
+    op = operators.OracleProblem(kind, n, 0.0, 1.0, omega, eps)
+    d = np.array([1.0, 0.0, 0.0])
+    pol = np.array([0.0, 0.0, 1.0])
+    b = torch.empty((3, n, n, n), dtype=torch.complex128, device="cuda:0")
+    P.rhs(d, pol if kind == "maxwell" else None, 1, b)
+    J = torch.zeros_like(b)
+    st, info = P.solve(b, J, tol=1e-12, max_inner=500, mode=vie.VIE_SOLVE_BICGSTAB)
+    Jo, io = solvers.bicgstab(op.apply, op.rhs(d, pol if kind == "maxwell" else None), tol=1e-12)
+    assert io["converged"] and info.rel_residual <= 1e-12
+    assert rel(J.cpu().numpy(), Jo) <= 1e-10
+    assert abs(info.applies_fp64 - io["applies"]) <= 2
+    P.close()
