@@ -119,6 +119,28 @@ int vie_problem_ncomp(const vie_problem* P);
  *   nrhs   >= 1.  Asynchronous on stream. */
 vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
 
+/* y = (I + B + K) x like vie_apply, for callers that cannot allocate device
+ * memory when they apply the operator: code being recorded into a CUDA graph by
+ * stream capture, solvers inside frameworks that own all device memory through
+ * their own arena, and latency-bound loops that must not take the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this
+ * is an interface addition.
+ *   Scratch: the padded intermediates live in one file-scope device array of
+ *   64 MiB per device (held by every GPU that loads the library until the
+ *   process exits).  Sizes whose workspace exceeds it return VIE_EINVAL; with 3
+ *   components and nrhs = 1 that allows n <= 77 in FP32 and n <= 61 in FP64.
+ *   The call allocates nothing: no cudaMalloc/cudaFree or allocating library
+ *   routine.  Its first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The z-pass schedule must already be chosen for this precision (vie_tune,
+ *   or one vie_apply), otherwise VIE_EINVAL.
+ *   Every call shares the array and leaves its contents behind (no pass reads
+ *   scratch it did not write first); calls that overlap on the GPU -- on
+ *   different streams or different handles -- race on it and must be ordered
+ *   by the caller.
+ *   x, y, precision, nrhs, stream: as for vie_apply. */
+vie_status vie_apply_static(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
+
 /* Right-hand sides for plane-wave (or uniform-field) incidence, FP64 complex,
  * [nrhs][c][n][n][n] into device buffer rhs_out.
  *   d  host, [nrhs][3]: Laplace: the applied field E0 (grad phi_in = -E0);

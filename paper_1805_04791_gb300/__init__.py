@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "VIE_OK", 1: "VIE_EINVAL", 2: "VIE_ENOMEM", 3: "VIE_ECUDA", 4
 
 EXPORTED = ("vie_problem_create", "vie_problem_ncomp", "vie_apply", "vie_rhs_plane_wave", "vie_solve",
             "vie_eval_scattered", "vie_problem_bytes", "vie_problem_destroy", "vie_last_error",
-            "vie_profile_begin", "vie_profile_end", "vie_tune")
+            "vie_profile_begin", "vie_profile_end", "vie_tune", "vie_apply_static")
 
 
 class VieError(RuntimeError):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.vie_profile_begin.restype = c_int
     lib.vie_profile_end.argtypes = [vp, ctypes.POINTER(c_double), c_int, ctypes.POINTER(c_int)]
     lib.vie_profile_end.restype = c_int
+    lib.vie_apply_static.argtypes = [vp, vp, vp, c_int, c_int, vp]
+    lib.vie_apply_static.restype = c_int
     lib.vie_tune.argtypes = [vp, c_int, ctypes.POINTER(c_int), vp]
     lib.vie_tune.restype = c_int
     lib.vie_last_error.argtypes = []
@@ -133,6 +135,11 @@ def vie_problem_ncomp(P) -> int:
 
 def vie_apply(P, x, y, precision: int, nrhs: int = 1, stream=None):
     return _check(load().vie_apply(P, _ptr(x), _ptr(y), precision, nrhs, _stream(stream)))
+
+
+def vie_apply_static(P, x, y, precision: int, nrhs: int = 1, stream=None):
+    """vie_apply with the scratch in the library's fixed device array (allocates nothing)."""
+    return _check(load().vie_apply_static(P, _ptr(x), _ptr(y), precision, nrhs, _stream(stream)))
 
 
 def vie_rhs_plane_wave(P, d, p, nrhs: int, rhs_out, stream=None):
