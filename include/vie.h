@@ -179,10 +179,15 @@ size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu);
  * handle was created with, and wait for that stream. */
 vie_status vie_problem_destroy(vie_problem* P);
 
-/* Autotune the z-pass schedule (pencils per CTA, one CTA per mirror group of
- * tiles or one per tile) of vie_apply at this precision by timing every
+/* Autotune the z-pass schedule of vie_apply at this precision by timing every
  * applicable variant on this device; the choice is kept in the handle and
- * written to *variant (-1: the shape uses the generic kernels).  vie_apply
+ * written to *variant (-1: the shape uses the generic kernels).  Variants:
+ * 0/1/2 one CTA per mirror group of tiles with 8/16/4 pencils per tile, one
+ * component per thread; 3 one CTA per tile of 8 pencils; 4/5/6 (FP32 only,
+ * 2n in {64, 96, 128, 256}) as 0/1/2 with two neighbouring pencils per
+ * thread packed as f32x2 lanes; 7/8/9 (FP32 only, same sizes) mirror-group
+ * CTAs of 8/4/16 pencils with all three components of a vector per thread.
+ * vie_apply
  * tunes on its first call for a precision anyway; calling vie_tune first keeps
  * the tuning time out of a timed or captured region.  Synchronises the stream.
  * Environment: VIE_TUNE=0 takes the first applicable variant without timing,

@@ -347,9 +347,11 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   int& p3v = P->p3_variant[sizeof(T) == 8 ? 0 : 1][K.mode];
   if (fs.p3 && p3v < 0) {
     // one decision per (n, precision, mode) per process: every problem of a
-    // shape then runs the same arithmetic (bitwise-reproducible results)
+    // shape then runs the same arithmetic (bitwise-reproducible results).  A
+    // variant forced with VIE_P3_VARIANT bypasses the cache both ways.
     const long long key = ((long long)P->n * 2 + (sizeof(T) == 8 ? 0 : 1)) * 8 + K.mode;
-    {
+    const bool forced = getenv("VIE_P3_VARIANT") != nullptr;
+    if (!forced) {
       std::lock_guard<std::mutex> g(tune_mutex());
       auto it = tune_cache().find(key);
       if (it != tune_cache().end()) p3v = it->second;
@@ -357,9 +359,11 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     if (p3v < 0) {
       vie_status e = tune_dispatch(P, K, B, C, sizeof(T) == 8, st, &p3v);
       if (e != VIE_OK) return e;
-      std::lock_guard<std::mutex> g(tune_mutex());
-      tune_cache().emplace(key, p3v);
-      p3v = tune_cache()[key];
+      if (!forced) {
+        std::lock_guard<std::mutex> g(tune_mutex());
+        tune_cache().emplace(key, p3v);
+        p3v = tune_cache()[key];
+      }
     }
   }
   if (p3v == kP3Generic) fs.p3 = false;

@@ -29,6 +29,33 @@ __device__ __forceinline__ void load_tw(V* tw, const V* __restrict__ twg, int M)
   for (int j = flat_tid(); j < M; j += flat_nthreads()) tw[j] = twg[j];
 }
 
+// Asynchronous global -> shared copy (cp.async, sm_80+): BYTES in {4, 8, 16},
+// both addresses aligned to BYTES.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Stage the kernel octant entries of a mirror group in shared memory as
+// slab[a][oz][q] (a < narr arrays, oz <= n, q < QW) from src[a O^3 + oz O^2 + q],
+// all copies in flight at once; the caller waits (cp_async_wait_all, then a
+// barrier) before reading the slab, and can do other work meanwhile.
+template <int QW, typename E>
+__device__ __forceinline__ void slab_async(E* slab, const E* src, int narr, int O, long long O3, int tid, int nthr) {
+  for (int a = 0; a < narr; ++a) {
+    const E* sa = src + a * O3;
+    E* da = slab + a * O * QW;
+    for (int idx = tid; idx < O * QW; idx += nthr) {
+      const int oz = idx / QW, q = idx - oz * QW;
+      cp_async<sizeof(E)>(da + idx, sa + (long long)oz * O * O + q);
+    }
+  }
+  cp_async_commit();
+}
+
 // ------------------------------------------------ register-resident fast path
 // For 2n = R1 * R2 in {64, 128, 256, 512} every line is transformed by R2
 // threads with one shared-memory transpose per direction (vie_fft2.cuh).
@@ -295,16 +322,9 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
   const int kyp = blockIdx.x / (NTX / 2), txp = blockIdx.x - (blockIdx.x / (NTX / 2)) * (NTX / 2);
   const int O = n + 1;
   const long long O3 = (long long)O * O * O;
+  // kernel slab copies in flight while tile 0 runs its forward transform
+  slab_async<QW>(slab, K + ((long long)kyp) * O + NP * txp, NARR, O, O3, threadIdx.x, NTHR);
   for (int j = threadIdx.x; j < M; j += NTHR) tw[j] = twg[j];
-  {
-    const int tot = NARR * O * QW;
-    const V* src = K + ((long long)kyp) * O + NP * txp;
-    for (int idx = threadIdx.x; idx < tot; idx += NTHR) {
-      const int q = idx % QW, r = idx / QW;
-      const int oz = r % O, a = r / O;
-      slab[idx] = src[a * O3 + (long long)oz * O * O + q];
-    }
-  }
   const int l = threadIdx.x % NP, t = (threadIdx.x / NP) % R2, c = threadIdx.x / (NP * R2);
   const int b0 = blockIdx.y;
   const long long zs = (long long)M * M, cs = (long long)n * zs;
@@ -339,6 +359,7 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
 #pragma unroll
           for (int k2 = 0; k2 < R2; ++k2) s[t + R2 * j + R1 * k2] = X[j][k2];
     }
+    cp_async_wait_all();  // the kernel slab (no-op after the first tile)
     __syncthreads();
     if (c < CO) {
       const bool fy = ky > n, fx = kx > n;
@@ -388,6 +409,316 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
       F::template invB<true>(u, t, s);
 #pragma unroll
       for (int n1 = 0; n1 < R1 / 2; ++n1) colbase[c * cs + (long long)(R2 * n1 + t) * zs] = u[n1];
+    }
+  }
+}
+
+// z-pencils, lane-pair variant (FP32 only).  Same mirror-group CTA and
+// kernel slab as f_p3c, but every thread carries two neighbouring pencils
+// (kx, kx + 1) of its component as the two lanes of f32x2 values: the FFT
+// codelets, the twiddle multiplies and the kernel mixing run as packed
+// instructions for both pencils at once, and every shared-memory transfer of
+// the transposes moves 16 bytes (both pencils' complex values).  The twiddle
+// table is stored lane-broadcast ({wr, wr}, {wi, wi}).
+template <int MODE, int NP, int R2>
+struct P3pThreads {
+  static constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
+  static constexpr int N = (NP / 2) * R2 * CMAX;
+  static constexpr int MINB = N <= 192 ? 2 : 1;
+};
+
+template <int R1, int R2, int MODE, int NP>
+__global__ void __launch_bounds__(P3pThreads<MODE, NP, R2>::N, P3pThreads<MODE, NP, R2>::MINB)
+f_p3p(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const float2* __restrict__ twg) {
+  typedef f32x2 T;
+  typedef c32x2 V;
+  typedef Fft2<T, R1, R2> F;
+  constexpr int CI = ModeDim<MODE>::CI, CO = ModeDim<MODE>::CO, NT = ModeDim<MODE>::NT;
+  constexpr int CMAX = CI > CO ? CI : CO;
+  constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
+  constexpr int M = F::M, NTX = M / NP, NQ = NP / 2, NTHR = NQ * R2 * CMAX;
+  constexpr int LS = ((F::LS0 + 13) / 16) * 16 + 2;  // 16-byte elements: LS = 2 mod 16
+  constexpr int QW = NP + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* tw = (V*)smraw;
+  V* sm = tw + M;
+  float2* slab = (float2*)(sm + CMAX * NQ * LS);
+  const int kyp = blockIdx.x / (NTX / 2), txp = blockIdx.x - (blockIdx.x / (NTX / 2)) * (NTX / 2);
+  const int O = n + 1;
+  const long long O3 = (long long)O * O * O;
+  // kernel slab copies in flight while tile 0 runs its forward transform
+  slab_async<QW>(slab, K + ((long long)kyp) * O + NP * txp, NARR, O, O3, threadIdx.x, NTHR);
+  for (int j = threadIdx.x; j < M; j += NTHR) {
+    const float2 w = twg[j];
+    tw[j] = CT<T>::make(T(w.x, w.x), T(w.y, w.y));
+  }
+  const int l = threadIdx.x % NQ, t = (threadIdx.x / NQ) % R2, c = threadIdx.x / (NQ * R2);
+  const int b0 = blockIdx.y;
+  const long long zs = (long long)M * M, cs = (long long)n * zs;
+  V* s = sm + (c * NQ + l) * LS;
+  int tb[NT], ta[NT], tsg[NT];
+  const int ntm = (c < CO) ? mix_terms<MODE>(c, tb, ta, tsg) : 0;
+  const bool self_y = (kyp == 0 || kyp == M / 2);
+#pragma unroll 1
+  for (int v = 0; v < 4; ++v) {
+    if ((v & 1) && self_y) continue;  // block-uniform
+    const int ky = (v & 1) ? M - kyp : kyp;
+    const int tile = (v & 2) ? NTX - 1 - txp : txp;
+    const int kx0 = tile * NP + 2 * l;  // lanes: kx0 and kx0 + 1 (kx0 even: 16-byte aligned pairs)
+    float2* colbase = B + (long long)b0 * C * cs + (long long)ky * M + kx0;
+    V X[F::J][R2];
+    V u[R1];
+    if (c < CI) {
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) {
+        if (n1 < R1 / 2) {
+          const float4 g = *(const float4*)(colbase + c * cs + (long long)(R2 * n1 + t) * zs);
+          u[n1] = CT<T>::make(T(g.x, g.z), T(g.y, g.w));
+        } else {
+          u[n1] = CT<T>::make(T(0.0), T(0.0));
+        }
+      }
+    }
+    __syncthreads();  // previous tile's readers of s are done; slab and tw are visible
+    if (c < CI) F::template fwd1<true>(u, t, s, tw);
+    __syncthreads();
+    if (c < CI) F::fwd2(X, t, s);
+    __syncthreads();
+    if (c < CI) {
+#pragma unroll
+      for (int j = 0; j < F::J; ++j)
+        if (F::row(t, j))
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) s[t + R2 * j + R1 * k2] = X[j][k2];
+    }
+    cp_async_wait_all();  // the kernel slab (no-op after the first tile)
+    __syncthreads();
+    if (c < CO) {
+      const bool fy = ky > n;
+      const bool fx0 = kx0 > n, fx1 = kx0 + 1 > n;
+      const int q0 = (fx0 ? M - kx0 : kx0) - NP * txp, q1 = (fx1 ? M - kx0 - 1 : kx0 + 1) - NP * txp;
+      T sg0[NT], sg1[NT];
+      const float2* kp[NT];
+      const V* xs[NT];
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        if (i >= ntm) break;
+        const int par = sym_parity(MODE == KM_DIV ? 6 + ta[i] : ta[i]);
+        const bool ny = ((par & 2) && fy) != (tsg[i] < 0);
+        const bool n0 = ny != ((par & 1) && fx0), n1 = ny != ((par & 1) && fx1);
+        const bool oz = (par & 4) != 0;
+        sg0[i] = T(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
+        sg1[i] = T((n0 != oz) ? -1.f : 1.f, (n1 != oz) ? -1.f : 1.f);
+        kp[i] = slab + ta[i] * O * QW;
+        xs[i] = sm + (tb[i] * NQ + l) * LS;
+      }
+#pragma unroll
+      for (int j = 0; j < F::J; ++j)
+        if (F::row(t, j))
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const int k = t + R2 * j + R1 * k2;
+            const bool fz = (k2 < R2 / 2) ? false : ((k2 > R2 / 2) ? true : (k > n));
+            const int zoff = (fz ? M - k : k) * QW;
+            T ax(0.0), ay(0.0);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+              if (i >= ntm) break;
+              const float2 k0 = kp[i][zoff + q0], k1 = kp[i][zoff + q1];
+              const T kr(k0.x, k1.x), ki(k0.y, k1.y);
+              const V xv = xs[i][k];
+              const T sgn = fz ? sg1[i] : sg0[i];
+              const T px = fmadd(kr, xv.x, -(ki * xv.y));
+              const T py = fmadd(kr, xv.y, ki * xv.x);
+              ax = fmadd(sgn, px, ax);
+              ay = fmadd(sgn, py, ay);
+            }
+            X[j][k2] = CT<T>::make(ax, ay);
+          }
+    }
+    __syncthreads();
+    if (c < CO) F::invA(X, t, s, tw);
+    __syncthreads();
+    if (c < CO) {
+      F::template invB<true>(u, t, s);
+#pragma unroll
+      for (int n1 = 0; n1 < R1 / 2; ++n1)
+        *(float4*)(colbase + c * cs + (long long)(R2 * n1 + t) * zs) =
+            make_float4(u[n1].x.a, u[n1].y.a, u[n1].x.b, u[n1].y.b);
+    }
+  }
+}
+
+// z-pencils, component-group variant (FP32 only).  Every thread carries all
+// three components of a vector (J, or M for Maxwell) on its pencil: the three
+// forward transforms share the twiddles (read once into registers), the kernel
+// mixing runs on registers and reads each kernel value of a point once for
+// all three outputs, and no spectrum is exchanged through shared memory
+// except the other vector's for the Maxwell curl terms (two groups per
+// pencil).  Shared-memory traffic per point is about half that of f_p3c.  The
+// next tile's inputs are loaded into registers while the current tile runs,
+// and the kernel slab is stored [array][x][z] with a row pitch of 2 mod 16
+// elements, so the mixing loads of 8 pencils x 2 threads hit distinct banks.
+template <int MODE, int NP, int R2>
+struct P3tThreads {
+  static constexpr int NG = (MODE == KM_MAXWELL6) ? 2 : 1;
+  static constexpr int N = NP * R2 * NG;
+};
+
+template <int R1, int R2, int MODE, int NP>
+__global__ void __launch_bounds__(P3tThreads<MODE, NP, R2>::N)
+f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const float2* __restrict__ twg) {
+  typedef float T;
+  typedef float2 V;
+  typedef Fft2<T, R1, R2> F;
+  constexpr int NG = P3tThreads<MODE, NP, R2>::NG;
+  constexpr int G = 3;                          // components per thread
+  constexpr int GO = (MODE == KM_DIV) ? 1 : 3;  // output components per thread
+  constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
+  constexpr int M = F::M, NTX = M / NP, NTHR = NP * R2 * NG, H = R1 / 2;
+  constexpr int LS = ((F::LS0 + 13) / 16) * 16 + 2;
+  constexpr int QW = NP + 1;
+  static_assert(MODE == KM_SYM3 || MODE == KM_DIV || MODE == KM_MAXWELL6, "component-group z pass");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* tw = (V*)smraw;
+  V* sm = tw + M;
+  V* slab = sm + NG * G * NP * LS;
+  const int kyp = blockIdx.x / (NTX / 2), txp = blockIdx.x - (blockIdx.x / (NTX / 2)) * (NTX / 2);
+  const int O = n + 1, OP = ((O + 13) / 16) * 16 + 2;
+  const long long O3 = (long long)O * O * O;
+  {
+    // kernel slab [a][q][oz] <- K[a][oz][kyp][NP txp + q], in flight during tile 0's forward transforms
+    const V* src = K + (long long)kyp * O + NP * txp;
+    for (int a = 0; a < NARR; ++a)
+      for (int idx = threadIdx.x; idx < O * QW; idx += NTHR) {
+        const int oz = idx / QW, q = idx - oz * QW;
+        cp_async<8>(slab + (a * QW + q) * OP + oz, src + a * O3 + (long long)oz * O * O + q);
+      }
+    cp_async_commit();
+  }
+  for (int j = threadIdx.x; j < M; j += NTHR) tw[j] = twg[j];
+  const int l = threadIdx.x % NP, t = (threadIdx.x / NP) % R2, h = threadIdx.x / (NP * R2);
+  const long long zs = (long long)M * M, cs = (long long)n * zs;
+  const int b0 = blockIdx.y;
+  const bool self_y = (kyp == 0 || kyp == M / 2);
+  const int ntiles = self_y ? 2 : 4;  // mirror tiles (ky, M - ky) x (kx tile, mirrored tile)
+  auto tile_ky = [&](int i) { const int v = self_y ? 2 * i : i; return (v & 1) ? M - kyp : kyp; };
+  auto tile_kx = [&](int i) { const int v = self_y ? 2 * i : i; return ((v & 2) ? NTX - 1 - txp : txp) * NP + l; };
+  V g[G][H];  // this (then the next) tile's inputs, z < n
+  {
+    const V* src = B + (long long)b0 * C * cs + (long long)tile_ky(0) * M + tile_kx(0) + (long long)(h * G) * cs;
+#pragma unroll
+    for (int c = 0; c < G; ++c)
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) g[c][n1] = src[c * cs + (long long)(R2 * n1 + t) * zs];
+  }
+#pragma unroll 1
+  for (int i = 0; i < ntiles; ++i) {
+    const int ky = tile_ky(i), kx = tile_kx(i);
+    V* colbase = B + (long long)b0 * C * cs + (long long)ky * M + kx;
+    V* s0 = sm + ((h * G) * NP + l) * LS;  // this group's transpose lines, component c at s0 + c NP LS
+    __syncthreads();                       // previous tile's readers of the transpose lines are done
+    {
+      V w[R1];
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) w[k1] = tw[t * k1];
+#pragma unroll
+      for (int c = 0; c < G; ++c) {
+        V u[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) u[n1] = (n1 < H) ? g[c][n1] : make_float2(0.f, 0.f);
+        F::template fwd1w<true>(u, t, s0 + c * NP * LS, w);
+      }
+    }
+    if (i + 1 < ntiles) {  // prefetch the next tile
+      const V* src = B + (long long)b0 * C * cs + (long long)tile_ky(i + 1) * M + tile_kx(i + 1) + (long long)(h * G) * cs;
+#pragma unroll
+      for (int c = 0; c < G; ++c)
+#pragma unroll
+        for (int n1 = 0; n1 < H; ++n1) g[c][n1] = src[c * cs + (long long)(R2 * n1 + t) * zs];
+    }
+    __syncthreads();
+    V X[G][F::J][R2];
+#pragma unroll
+    for (int c = 0; c < G; ++c) F::fwd2(X[c], t, s0 + c * NP * LS);
+    cp_async_wait_all();  // the kernel slab (no-op after the first tile)
+    __syncthreads();      // transpose lines free again; slab visible
+    const V* so = sm + (((1 - h) * G) * NP + l) * LS;  // the other group's parked spectra (Maxwell)
+    if (NG == 2) {
+#pragma unroll
+      for (int c = 0; c < G; ++c)
+#pragma unroll
+        for (int j = 0; j < F::J; ++j)
+          if (F::row(t, j))
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) s0[c * NP * LS + t + R2 * j + R1 * k2] = X[c][j][k2];
+      __syncthreads();
+    }
+    {
+      const bool fy = ky > n, fx = kx > n;
+      const V* kq = slab + ((fx ? M - kx : kx) - NP * txp) * OP;
+      T sg0[NARR], sg1[NARR];
+#pragma unroll
+      for (int a = 0; a < NARR; ++a) {
+        const int par = sym_parity(MODE == KM_DIV ? 6 + a : a);
+        const bool ng = ((par & 2) && fy) != ((par & 1) && fx);
+        sg0[a] = ng ? -1.f : 1.f;
+        sg1[a] = (ng != ((par & 4) != 0)) ? -1.f : 1.f;
+      }
+#pragma unroll
+      for (int j = 0; j < F::J; ++j)
+        if (F::row(t, j))
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const int k = t + R2 * j + R1 * k2;
+            const bool fz = (k2 < R2 / 2) ? false : ((k2 > R2 / 2) ? true : (k > n));
+            const int zo = fz ? M - k : k;
+            V kv[NARR];
+#pragma unroll
+            for (int a = 0; a < NARR; ++a) {
+              kv[a] = kq[a * QW * OP + zo];
+              if (sym_parity(MODE == KM_DIV ? 6 + a : a) != 0) kv[a] = (fz ? sg1[a] : sg0[a]) * kv[a];
+            }
+            const V x0 = X[0][j][k2], x1 = X[1][j][k2], x2 = X[2][j][k2];
+            if (MODE == KM_DIV) {
+              X[0][j][k2] = cmul(kv[0], x0) + cmul(kv[1], x1) + cmul(kv[2], x2);
+            } else {
+              // symmetric 3x3: xx yy zz xy xz yz
+              V y0 = cmul(kv[0], x0) + cmul(kv[3], x1) + cmul(kv[4], x2);
+              V y1 = cmul(kv[3], x0) + cmul(kv[1], x1) + cmul(kv[5], x2);
+              V y2 = cmul(kv[4], x0) + cmul(kv[5], x1) + cmul(kv[2], x2);
+              if (MODE == KM_MAXWELL6) {
+                // J rows + (P x M), M rows - (P x J); P_a = kernel 6 + a, the other vector from shared memory
+                const V o0 = so[k], o1 = so[NP * LS + k], o2 = so[2 * NP * LS + k];
+                V c0 = cmul(kv[7], o2) - cmul(kv[8], o1);
+                V c1 = cmul(kv[8], o0) - cmul(kv[6], o2);
+                V c2 = cmul(kv[6], o1) - cmul(kv[7], o0);
+                if (h == 0) {
+                  y0 = y0 + c0;
+                  y1 = y1 + c1;
+                  y2 = y2 + c2;
+                } else {
+                  y0 = y0 - c0;
+                  y1 = y1 - c1;
+                  y2 = y2 - c2;
+                }
+              }
+              X[0][j][k2] = y0;
+              X[1][j][k2] = y1;
+              X[2][j][k2] = y2;
+            }
+          }
+    }
+    if (NG == 2) __syncthreads();  // the other group has read the parked spectra
+#pragma unroll
+    for (int c = 0; c < GO; ++c) F::invA(X[c], t, s0 + c * NP * LS, tw);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < GO; ++c) {
+      V u[R1];
+      F::template invB<true>(u, t, s0 + c * NP * LS);
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) colbase[(h * G + c) * cs + (long long)(R2 * n1 + t) * zs] = u[n1];
     }
   }
 }
@@ -466,6 +797,7 @@ inline size_t smem_optin() { return (size_t)smem_optin_bytes(); }
 template <typename T, int R1, int R2>
 struct FastPath {
   typedef typename CT<T>::V V;
+  typedef Fft2<f32x2, R1, R2> F2;
   static constexpr int M = R1 * R2, L = 256 / R2;
   static size_t smem() { return sizeof(V) * (M + L * Fft2<T, R1, R2>::LS); }
   static vie_status p1(const V* x, V* A, int n, int C, int cin, int nrhs, const V* tw, cudaStream_t st) {
@@ -518,6 +850,60 @@ struct FastPath {
     }
   }
   template <int MODE, int NP>
+  static vie_status p3p(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
+    *done = false;
+    if constexpr (sizeof(T) != 4 || NP < 2 || F2::J * R2 > 16 || R1 > 16) {
+      return VIE_OK;  // lane pairs are FP32 only; register budget limits the line length
+    } else {
+      constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
+      constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
+      constexpr int LS = ((F2::LS0 + 13) / 16) * 16 + 2;
+      constexpr int NTX = M / NP;
+      constexpr int NTHR = P3pThreads<MODE, NP, R2>::N;
+      const size_t sm = 16 * (M + (size_t)CMAX * (NP / 2) * LS) + 8 * (size_t)NARR * (n + 1) * (NP + 1);
+      const size_t cap = P3pThreads<MODE, NP, R2>::MINB == 2 ? 112 * 1024 : 224 * 1024;
+      if constexpr (NTHR > 1024 || NTX < 2) {
+        return VIE_OK;
+      } else {
+        if (sm > cap || sm > smem_optin()) return VIE_OK;
+        VIE_CK(allow_smem(f_p3p<R1, R2, MODE, NP>));
+        f_p3p<R1, R2, MODE, NP><<<dim3((M / 2 + 1) * (NTX / 2), nrhs), NTHR, sm, st>>>(
+            (float2*)B, n, C, (const float2*)K, (const float2*)tw);
+        VIE_CK(cudaGetLastError());
+        *done = true;
+        return VIE_OK;
+      }
+    }
+  }
+  template <int MODE, int NP>
+  static vie_status p3t(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
+    *done = false;
+    if constexpr (sizeof(T) != 4 || Fft2<T, R1, R2>::J * R2 > 16 || R1 > 16 ||
+                  !(MODE == KM_SYM3 || MODE == KM_DIV || MODE == KM_MAXWELL6)) {
+      return VIE_OK;  // FP32 only; three components of a pencil must fit in registers
+    } else {
+      typedef Fft2<T, R1, R2> F;
+      constexpr int NG = P3tThreads<MODE, NP, R2>::NG;
+      constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
+      constexpr int LS = ((F::LS0 + 13) / 16) * 16 + 2;
+      constexpr int NTX = M / NP;
+      constexpr int NTHR = P3tThreads<MODE, NP, R2>::N;
+      const int O = n + 1, OP = ((O + 13) / 16) * 16 + 2;
+      const size_t sm = sizeof(V) * (M + (size_t)NG * 3 * NP * LS + (size_t)NARR * (NP + 1) * OP);
+      if constexpr (NTHR > 1024 || NTX < 2) {
+        return VIE_OK;
+      } else {
+        if (sm > smem_optin()) return VIE_OK;
+        VIE_CK(allow_smem(f_p3t<R1, R2, MODE, NP>));
+        f_p3t<R1, R2, MODE, NP><<<dim3((M / 2 + 1) * (NTX / 2), nrhs), NTHR, sm, st>>>(
+            (float2*)B, n, C, (const float2*)K, (const float2*)tw);
+        VIE_CK(cudaGetLastError());
+        *done = true;
+        return VIE_OK;
+      }
+    }
+  }
+  template <int MODE, int NP>
   static vie_status p3b_ok(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
     constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
     *done = false;
@@ -537,7 +923,13 @@ struct FastPath {
       case 0: return p3c<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
       case 1: return p3c<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
       case 2: return p3c<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
-      default: return p3b_ok<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
+      case 3: return p3b_ok<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
+      case 4: return p3p<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
+      case 5: return p3p<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
+      case 6: return p3p<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
+      case 7: return p3t<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
+      case 8: return p3t<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
+      default: return p3t<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
     }
   }
   // Run P3 variant `variant` (0..kP3Variants-1); *done = false if it does not apply to this shape.
@@ -594,12 +986,14 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
 }
 
 // Autotuner for the z pass: every applicable variant (mirror-group CTAs with
-// 8, 16 or 4 pencils, or one tile per CTA with 8 pencils) is launched once
+// 8, 16 or 4 pencils, one tile per CTA with 8 pencils, lane-pair
+// mirror-group CTAs with 8, 16 or 4 pencils, or component-group mirror-group
+// CTAs with 8, 4 or 16 pencils) is launched once
 // to warm up and then timed over 3 launches with CUDA events on the buffer B
 // (whose contents are scratch at this point); the fastest is kept for the
 // problem's (precision, mode).  VIE_TUNE=0 takes the first applicable variant;
 // VIE_P3_VARIANT=k forces variant k.
-static const int kP3Variants = 4;
+static const int kP3Variants = 10;
 static const int kP3Generic = 99;
 
 template <typename T, int R1, int R2>

@@ -20,39 +20,26 @@ __host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { re
 __host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 // FP32 complex add/sub/scale as one packed f32x2 instruction on sm_100+
 // (element-wise IEEE round-to-nearest: bit-identical to two scalar ops, half
-// the issue slots -- the FFT butterflies are mostly complex adds).
+// the issue slots -- the FFT butterflies are mostly complex adds).  The
+// compiler builtins keep the operations visible to register allocation and
+// scheduling.
 __host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
-  float2 d;
-  asm("{.reg .b64 ra, rb, rd;\n\t mov.b64 ra, {%2, %3};\n\t mov.b64 rb, {%4, %5};\n\t"
-      " add.rn.f32x2 rd, ra, rb;\n\t mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
+  return __fadd2_rn(a, b);
 #else
   return make_float2(a.x + b.x, a.y + b.y);
 #endif
 }
 __host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
-  float2 d;
-  asm("{.reg .b64 ra, rb, rd;\n\t mov.b64 ra, {%2, %3};\n\t mov.b64 rb, {%4, %5};\n\t"
-      " sub.rn.f32x2 rd, ra, rb;\n\t mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a + (-1) b: one rounding, same as a - b
 #else
   return make_float2(a.x - b.x, a.y - b.y);
 #endif
 }
 __host__ __device__ __forceinline__ float2 operator*(float s, float2 a) {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
-  float2 d;
-  asm("{.reg .b64 ra, rb, rd;\n\t mov.b64 ra, {%2, %3};\n\t mov.b64 rb, {%4, %4};\n\t"
-      " mul.rn.f32x2 rd, ra, rb;\n\t mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(s));
-  return d;
+  return __fmul2_rn(make_float2(s, s), a);
 #else
   return make_float2(s * a.x, s * a.y);
 #endif
@@ -82,11 +69,83 @@ template <> struct CT<float> {
   static __host__ __device__ __forceinline__ V make(float a, float b) { return make_float2(a, b); }
 };
 
+// ------------------------------------------------ lane pairs: two lines at once
+// f32x2 holds the same quantity of two independent transforms (its lanes a
+// and b); c32x2 is a complex number whose real and imaginary parts are such
+// pairs.  Every arithmetic operation on them is one packed f32x2 instruction
+// (sm_100 and later), so a codelet instantiated on f32x2 transforms two lines
+// for the instruction count of one, and a multiplication by +-i is a swap of
+// register roles rather than arithmetic.  Each lane is rounded exactly as the
+// scalar operation would be.
+struct __align__(8) f32x2 {
+  float a, b;
+  f32x2() = default;
+  __host__ __device__ constexpr f32x2(float x, float y) : a(x), b(y) {}
+  __host__ __device__ constexpr f32x2(double s) : a((float)s), b((float)s) {}  // broadcast
+};
+struct __align__(16) c32x2 {
+  f32x2 x, y;
+};
+template <> struct CT<f32x2> {
+  typedef c32x2 V;
+  static __device__ __forceinline__ V make(f32x2 a, f32x2 b) {
+    V r;
+    r.x = a;
+    r.y = b;
+    return r;
+  }
+};
+__device__ __forceinline__ float2 f2(f32x2 v) { return make_float2(v.a, v.b); }
+__device__ __forceinline__ f32x2 p2(float2 v) { return f32x2(v.x, v.y); }
+__device__ __forceinline__ f32x2 operator+(f32x2 x, f32x2 y) { return p2(__fadd2_rn(f2(x), f2(y))); }
+// x - y as x + (-1) y: one rounding, identical to a subtraction
+__device__ __forceinline__ f32x2 operator-(f32x2 x, f32x2 y) {
+  return p2(__ffma2_rn(f2(y), make_float2(-1.f, -1.f), f2(x)));
+}
+__device__ __forceinline__ f32x2 operator*(f32x2 x, f32x2 y) { return p2(__fmul2_rn(f2(x), f2(y))); }
+__device__ __forceinline__ f32x2 operator-(f32x2 x) { return f32x2(-x.a, -x.b); }
+__device__ __forceinline__ f32x2& operator+=(f32x2& x, f32x2 y) {
+  x = x + y;
+  return x;
+}
+__device__ __forceinline__ c32x2 operator+(c32x2 a, c32x2 b) { return CT<f32x2>::make(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ c32x2 operator-(c32x2 a, c32x2 b) { return CT<f32x2>::make(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ c32x2 operator*(f32x2 s, c32x2 a) { return CT<f32x2>::make(s * a.x, s * a.y); }
+
+// a * b + c with one rounding
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ f32x2 fmadd(f32x2 a, f32x2 b, f32x2 c) { return p2(__ffma2_rn(f2(a), f2(b), f2(c))); }
+
+__device__ __forceinline__ c32x2 cmul(c32x2 a, c32x2 b) {
+  return CT<f32x2>::make(fmadd(a.x, b.x, -(a.y * b.y)), fmadd(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ c32x2 cmulc(c32x2 a, c32x2 b) {
+  return CT<f32x2>::make(fmadd(a.x, b.x, a.y * b.y), fmadd(a.y, b.x, -(a.x * b.y)));
+}
+
 // a * (S i) for S = +1 / -1
 template <int S, typename V>
 __device__ __forceinline__ V mul_si(V a) {
   V r;
   if (S > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+// a + S i b  and  a - S i b (no negation needed on any element type)
+template <int S, typename V>
+__device__ __forceinline__ V addi(V a, V b) {
+  V r;
+  if (S > 0) { r.x = a.x - b.y; r.y = a.y + b.x; } else { r.x = a.x + b.y; r.y = a.y - b.x; }
+  return r;
+}
+template <int S, typename V>
+__device__ __forceinline__ V subi(V a, V b) { return addi<-S>(a, b); }
+// a (c + i s) for real c, s
+template <typename T, typename V>
+__device__ __forceinline__ V rot(V a, T c, T s) {
+  V r;
+  r.x = fmadd(-s, a.y, c * a.x);
+  r.y = fmadd(s, a.x, c * a.y);
   return r;
 }
 
@@ -108,11 +167,11 @@ template <int S, typename T> struct Dft<3, S, T> {
   static __device__ __forceinline__ void run(V* u) {
     const T h3 = (T)0.86602540378443864676;  // sqrt(3)/2
     V t = u[1] + u[2];
-    V m = u[0] - (T)0.5 * t;
-    V d = mul_si<S>(h3 * (u[1] - u[2]));
+    V m = CT<T>::make(fmadd((T)-0.5, t.x, u[0].x), fmadd((T)-0.5, t.y, u[0].y));
+    V d = h3 * (u[1] - u[2]);
     u[0] = u[0] + t;
-    u[1] = m + d;
-    u[2] = m - d;
+    u[1] = addi<S>(m, d);
+    u[2] = subi<S>(m, d);
   }
 };
 
@@ -120,11 +179,11 @@ template <int S, typename T> struct Dft<4, S, T> {
   typedef typename CT<T>::V V;
   static __device__ __forceinline__ void run(V* u) {
     V a0 = u[0] + u[2], a1 = u[0] - u[2];
-    V b0 = u[1] + u[3], b1 = mul_si<S>(u[1] - u[3]);
+    V b0 = u[1] + u[3], b1 = u[1] - u[3];
     u[0] = a0 + b0;
     u[2] = a0 - b0;
-    u[1] = a1 + b1;
-    u[3] = a1 - b1;
+    u[1] = addi<S>(a1, b1);
+    u[3] = subi<S>(a1, b1);
   }
 };
 
@@ -136,18 +195,17 @@ template <int S, typename T> struct Dft<8, S, T> {
     V o[4] = {u[1], u[3], u[5], u[7]};
     Dft<4, S, T>::run(e);
     Dft<4, S, T>::run(o);
-    // w8^q = exp(S 2 pi i q / 8)
-    V o1 = CT<T>::make(r2 * (o[1].x - (T)S * o[1].y), r2 * (o[1].y + (T)S * o[1].x));  // (1 + S i)/sqrt2
-    V o2 = mul_si<S>(o[2]);
-    V o3 = CT<T>::make(r2 * (-o[3].x - (T)S * o[3].y), r2 * (-o[3].y + (T)S * o[3].x));  // (-1 + S i)/sqrt2
+    // w8^q = exp(S 2 pi i q / 8): w8 = (1 + S i)/sqrt2, w8^2 = S i, w8^3 = S i w8
+    V o1 = r2 * addi<S>(o[1], o[1]);
+    V o3 = r2 * addi<S>(o[3], o[3]);
     u[0] = e[0] + o[0];
     u[4] = e[0] - o[0];
     u[1] = e[1] + o1;
     u[5] = e[1] - o1;
-    u[2] = e[2] + o2;
-    u[6] = e[2] - o2;
-    u[3] = e[3] + o3;
-    u[7] = e[3] - o3;
+    u[2] = addi<S>(e[2], o[2]);
+    u[6] = subi<S>(e[2], o[2]);
+    u[3] = addi<S>(e[3], o3);
+    u[7] = subi<S>(e[3], o3);
   }
 };
 
@@ -176,8 +234,8 @@ template <int S, typename T> struct Dft<16, S, T> {
           a[q1][r2] = t[q1];
         } else {
           const T c = (T)cos_pi8(j);
-          const T s = (T)S * (T)cos_pi8(j + 12);  // sin(pi j/8) = cos(pi (j - 4)/8) = cos(pi (j+12)/8)
-          a[q1][r2] = CT<T>::make(c * t[q1].x - s * t[q1].y, c * t[q1].y + s * t[q1].x);
+          const T s = (T)(S * cos_pi8(j + 12));  // sin(pi j/8) = cos(pi (j - 4)/8) = cos(pi (j+12)/8)
+          a[q1][r2] = rot(t[q1], c, s);
         }
       }
     }
@@ -245,20 +303,24 @@ struct DftOdd {
     u[0] = sum;
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
-      T ax = u0.x, ay = u0.y, bx = 0, by = 0;
+      V A = u0, B;
 #pragma unroll
       for (int r = 1; r <= H; ++r) {
         int j = (r * q) % R;
         const T cs = (T)OddRoots<R>::c(j <= H ? j : R - j);
-        const T sn = (j <= H) ? (T)OddRoots<R>::s(j) : -(T)OddRoots<R>::s(R - j);
-        ax += cs * a[r].x;
-        ay += cs * a[r].y;
-        bx += sn * b[r].x;
-        by += sn * b[r].y;
+        const T sn = (T)((j <= H) ? OddRoots<R>::s(j) : -OddRoots<R>::s(R - j));
+        A.x = fmadd(cs, a[r].x, A.x);
+        A.y = fmadd(cs, a[r].y, A.y);
+        if (r == 1) {
+          B.x = sn * b[r].x;
+          B.y = sn * b[r].y;
+        } else {
+          B.x = fmadd(sn, b[r].x, B.x);
+          B.y = fmadd(sn, b[r].y, B.y);
+        }
       }
-      // S i B = (-S by, S bx)
-      u[q] = CT<T>::make(ax - (T)S * by, ay + (T)S * bx);
-      u[R - q] = CT<T>::make(ax + (T)S * by, ay - (T)S * bx);
+      u[q] = addi<S>(A, B);
+      u[R - q] = subi<S>(A, B);
     }
   }
 };

@@ -91,18 +91,18 @@ __device__ __forceinline__ double cos_2pi24(int j) {
 // a * W_R^{S j} with W_R = exp(2 pi i / R) (R divides 32 or 24)
 template <int R, int S, typename T>
 __device__ __forceinline__ typename CT<T>::V twc(typename CT<T>::V a, int j) {
-  T c, s;
+  double c, s;
   if constexpr (32 % R == 0) {
     const int q = (j * (32 / R)) & 31;  // angle pi q / 16
-    c = (T)cos_pi16(q);
-    s = (T)S * (T)cos_pi16(q + 24);  // sin(pi q/16) = cos(pi (q - 8)/16)
+    c = cos_pi16(q);
+    s = S * cos_pi16(q + 24);  // sin(pi q/16) = cos(pi (q - 8)/16)
   } else {
     static_assert(24 % R == 0, "twiddle table covers R | 32 and R | 24");
     const int q = (j * (24 / R)) % 24;  // angle 2 pi q / 24
-    c = (T)cos_2pi24(q);
-    s = (T)S * (T)cos_2pi24(q + 18);  // sin(t) = cos(t - pi/2)
+    c = cos_2pi24(q);
+    s = S * cos_2pi24(q + 18);  // sin(t) = cos(t - pi/2)
   }
-  return CT<T>::make(c * a.x - s * a.y, c * a.y + s * a.x);
+  return rot(a, (T)c, (T)s);
 }
 
 // DFT of length P Q on registers by the same two-step split as the line FFT:
@@ -215,6 +215,18 @@ struct Fft2 {
     for (int k1 = 0; k1 < R1; ++k1) {
       V v = u[k1];
       if (k1 != 0) v = cmul(v, tw[t * k1]);
+      s[k1 * PF + t] = v;
+    }
+  }
+  // Step 1 forward with the twiddles W_M^{t k1} already in registers (w[k1]).
+  template <bool HALF>
+  static __device__ __forceinline__ void fwd1w(V* u, int t, V* s, const V* w) {
+    if (HALF) dft_half_in<R1, -1, T>(u);
+    else Dft<R1, -1, T>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      V v = u[k1];
+      if (k1 != 0) v = cmul(v, w[k1]);
       s[k1 * PF + t] = v;
     }
   }
