@@ -61,9 +61,14 @@ typedef enum {
 
 typedef enum { VIE_LAPLACE = 0, VIE_HELMHOLTZ = 1, VIE_MAXWELL = 2 } vie_kind;
 
-/* Arithmetic of an operator apply: FP64 complex, or FP32 complex (inner
- * iterations of the mixed-precision solve). */
-typedef enum { VIE_FP64 = 0, VIE_FP32 = 1 } vie_precision;
+/* Arithmetic of an operator apply: FP64 complex; FP32 complex (inner
+ * iterations of the mixed-precision solve); or VIE_DF64: FP64 complex vectors
+ * in and out, arithmetic in double-word form (each real held as the unevaluated
+ * sum of two FP32 values, about 48 significant bits; relative error of the
+ * apply near 1e-13), which the mixed solve uses for its refinement residuals
+ * because it runs on the FP32 pipes.  Not a source of the paper's method: an
+ * implementation choice for the FP64 residual of Sec. 5's solve. */
+typedef enum { VIE_FP64 = 0, VIE_FP32 = 1, VIE_DF64 = 2 } vie_precision;
 
 /* Solver modes for vie_solve: plain FP64 GMRES(m); FP32-inner GMRES(m)
  * inside an FP64 iterative-refinement loop; or FP64 Bi-CGStab, the solver of
@@ -78,7 +83,9 @@ typedef struct {
   int restart;       /* GMRES restart length m (1..200) */
   int max_outer;     /* mixed: maximum refinement steps; FP64: maximum restarts */
   int max_inner;     /* maximum GMRES iterations per refinement step (mixed) or in total (FP64) */
-  double inner_tol;  /* mixed: relative tolerance of each inner FP32 solve */
+  double inner_tol;  /* mixed: each inner FP32 solve stops at inner_tol ||r|| or at
+                        0.25 tol ||b||, whichever is larger (later refinement
+                        steps need only reach the overall target) */
   int mode;          /* vie_solve_mode */
   int nrhs;          /* number of right-hand sides, solved independently (>= 1) */
 } vie_solve_opts;
@@ -87,7 +94,8 @@ typedef struct {
   int outer_iters;        /* refinement steps (mixed) or restarts (FP64) */
   int inner_iters;        /* GMRES iterations (= FP32 or FP64 applies inside Arnoldi) */
   int applies_fp32;
-  int applies_fp64;
+  int applies_fp64;       /* FP64-accuracy applies: native FP64, or VIE_DF64 for the mixed
+                             mode's refinement residuals (VIE_RESIDUAL_FP64=1: native) */
   double rel_residual;    /* max over right-hand sides of the final FP64 relative residual */
   double t_solve;         /* wall seconds spent in vie_solve */
 } vie_solve_info;
@@ -114,9 +122,11 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
 int vie_problem_ncomp(const vie_problem* P);
 
 /* y = (I + B + K) x, the left-hand side of Eq. (eq:intLap), (eq:intH) or (eq:intM).
- *   x, y   device, [nrhs][c][n][n][n], FP64 complex (precision VIE_FP64) or FP32
- *          complex (VIE_FP32); x and y must not overlap.
- *   nrhs   >= 1.  Asynchronous on stream. */
+ *   x, y   device, [nrhs][c][n][n][n], FP64 complex (precision VIE_FP64 or
+ *          VIE_DF64) or FP32 complex (VIE_FP32); x and y must not overlap.
+ *   nrhs   >= 1.  Asynchronous on stream.  The first VIE_DF64 apply of a
+ *   handle converts its tables to double-word form (device memory of the size
+ *   of the FP64 kernel and medium tables, kept until destroy). */
 vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
 
 /* y = (I + B + K) x like vie_apply, for callers that cannot allocate device

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libvie_gb300.so")
 
 VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA, VIE_ENOCONV, VIE_ENAN, VIE_ETIMEOUT, VIE_EBUSY = range(8)
 VIE_LAPLACE, VIE_HELMHOLTZ, VIE_MAXWELL = range(3)
-VIE_FP64, VIE_FP32 = 0, 1
+VIE_FP64, VIE_FP32, VIE_DF64 = 0, 1, 2  # VIE_DF64: FP64 vectors, double-word arithmetic
 VIE_SOLVE_FP64, VIE_SOLVE_MIXED, VIE_SOLVE_BICGSTAB = 0, 1, 2
 P3_VARIANTS = 10  # z-pass schedules vie_tune chooses from (include/vie.h)
 KINDS = {"laplace": VIE_LAPLACE, "helmholtz": VIE_HELMHOLTZ, "maxwell": VIE_MAXWELL}

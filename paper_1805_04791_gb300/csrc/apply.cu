@@ -28,7 +28,7 @@ namespace vie {
 // twiddle table staged in shared memory (vie_fft.cuh).
 // ---------------------------------------------------------------- P1
 template <typename T>
-__global__ void k_p1(const typename CT<T>::V* __restrict__ x, typename CT<T>::V* __restrict__ A, int n, FftPlan pl,
+__global__ void k_p1(const typename IOT<T>::E* __restrict__ x, typename CT<T>::V* __restrict__ A, int n, FftPlan pl,
                      const typename CT<T>::V* __restrict__ twg, int nl, int C) {
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -39,14 +39,14 @@ __global__ void k_p1(const typename CT<T>::V* __restrict__ x, typename CT<T>::V*
   load_tw(tw, twg, M);
   const long long N = (long long)n * n * n;
   const int c = blockIdx.y, b = blockIdx.z, nc = gridDim.y;
-  const V* src = x + ((long long)b * nc + c) * N;
+  const typename IOT<T>::E* src = x + ((long long)b * nc + c) * N;
   V* dst = A + ((long long)b * C + c) * ((long long)n * n * M);
   const int r0 = blockIdx.x * nl;
   const int rows = n * n;
   for (int l = threadIdx.y; l < nl; l += blockDim.y) {
     const int r = r0 + l;
     for (int j = threadIdx.x; j < M; j += blockDim.x)
-      b0[l * LS + j] = (j < n && r < rows) ? src[(long long)r * n + j] : CT<T>::make(0, 0);
+      b0[l * LS + j] = (j < n && r < rows) ? to_v<T>(src[(long long)r * n + j]) : CT<T>::make(0, 0);
   }
   __syncthreads();
   V* res = tile_fft<-1, T>(b0, b1, pl, tw, nl, LS);
@@ -191,8 +191,8 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
 
 // ---------------------------------------------------------------- P5
 template <typename T>
-__global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename CT<T>::V* __restrict__ xin,
-                     typename CT<T>::V* __restrict__ y, int n, FftPlan pl, const typename CT<T>::V* __restrict__ twg,
+__global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename IOT<T>::E* __restrict__ xin,
+                     typename IOT<T>::E* __restrict__ y, int n, FftPlan pl, const typename CT<T>::V* __restrict__ twg,
                      int nr, int C, int cout, const typename CT<T>::V* __restrict__ He,
                      const typename CT<T>::V* __restrict__ Hm, int with_identity) {
   typedef typename CT<T>::V V;
@@ -227,15 +227,15 @@ __global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename CT<
         const V* H = blk == 0 ? He : Hm;
         const V hxx = H[0 * N + pt], hyy = H[1 * N + pt], hzz = H[2 * N + pt];
         const V hxy = H[3 * N + pt], hxz = H[4 * N + pt], hyz = H[5 * N + pt];
-        const V* xi = xin + ((long long)b * cout + 3 * blk) * N + pt;
-        V* yo = y + ((long long)b * cout + 3 * blk) * N + pt;
+        const typename IOT<T>::E* xi = xin + ((long long)b * cout + 3 * blk) * N + pt;
+        typename IOT<T>::E* yo = y + ((long long)b * cout + 3 * blk) * N + pt;
         const V a0 = u[3 * blk], a1 = u[3 * blk + 1], a2 = u[3 * blk + 2];
-        yo[0] = xi[0] + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2);
-        yo[N] = xi[N] + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2);
-        yo[2 * N] = xi[2 * N] + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2);
+        yo[0] = from_v<T>(to_v<T>(xi[0]) + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
+        yo[N] = from_v<T>(to_v<T>(xi[N]) + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
+        yo[2 * N] = from_v<T>(to_v<T>(xi[2 * N]) + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
       }
     } else {
-      for (int c = 0; c < cout; ++c) y[((long long)b * cout + c) * N + pt] = u[c];
+      for (int c = 0; c < cout; ++c) y[((long long)b * cout + c) * N + pt] = from_v<T>(u[c]);
     }
   }
 }
@@ -254,7 +254,7 @@ static dim3 line_block(int M) {
 }
 
 size_t apply_workspace_bytes(int n, int c, int nrhs, int prec) {
-  const size_t esz = prec == VIE_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t esz = prec == VIE_FP32 ? sizeof(float2) : sizeof(double2);  // double-word complex is 16 bytes too
   const size_t M = 2 * (size_t)n;
   return esz * (size_t)nrhs * c * ((size_t)n * n * M + (size_t)n * M * M);
 }
@@ -287,21 +287,21 @@ static std::map<long long, int>& tune_cache() {
 
 
 static vie_status fast_dispatch(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                                bool with_identity, void* A, void* B, int C, bool f64, cudaStream_t st) {
+                                bool with_identity, void* A, void* B, int C, int prec, cudaStream_t st) {
   switch (2 * P->n) {
 #define VIE_CASE(MM, RA, RB) \
-  case MM: return fast_pass_##MM(f64, pass, P, K, in, out, nrhs, with_identity, A, B, C, st);
+  case MM: return fast_pass_##MM(prec == VIE_FP64, pass, P, K, in, out, nrhs, with_identity, A, B, C, st);
     VIE_FAST_SIZES(VIE_CASE)
 #undef VIE_CASE
     default: set_error("no fast path for this size"); return VIE_EINVAL;
   }
 }
 
-static vie_status tune_dispatch(vie_problem* P, const KernelSet& K, void* B, int C, bool f64, cudaStream_t st,
+static vie_status tune_dispatch(vie_problem* P, const KernelSet& K, void* B, int C, int prec, cudaStream_t st,
                                 int* best) {
   switch (2 * P->n) {
 #define VIE_CASE(MM, RA, RB) \
-  case MM: return tune_p3_##MM(f64, P, K, B, C, st, best);
+  case MM: return tune_p3_##MM(prec == VIE_FP64, P, K, B, C, st, best);
     VIE_FAST_SIZES(VIE_CASE)
 #undef VIE_CASE
     default: set_error("no fast path for this size"); return VIE_EINVAL;
@@ -315,7 +315,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   const int n = P->n, M = 2 * n;
   const int cin = cin_of(K.mode), cout = cout_of(K.mode);
   const int C = std::max(cin, cout);
-  const size_t need = apply_workspace_bytes(n, C, nrhs, sizeof(T) == 8 ? VIE_FP64 : VIE_FP32);
+  const size_t need = apply_workspace_bytes(n, C, nrhs, Prec<T>::id);
   if (P->ws.bytes < need) {
     dfree(P->ws.buf, st);  // stream-ordered: earlier work on st completes first
     P->ws.buf = nullptr;
@@ -343,13 +343,15 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     ++pf.count;
   }
 
-  FastSel fs = fast_select(M, K.mode, with_identity);
-  int& p3v = P->p3_variant[sizeof(T) == 8 ? 0 : 1][K.mode];
+  // double-word arithmetic runs on the generic kernels only: its fully
+  // unrolled register-resident variants take far too long to compile
+  FastSel fs = (Prec<T>::id == VIE_DF64) ? FastSel() : fast_select(M, K.mode, with_identity);
+  int& p3v = P->p3_variant[Prec<T>::id][K.mode];
   if (fs.p3 && p3v < 0) {
     // one decision per (n, precision, mode) per process: every problem of a
     // shape then runs the same arithmetic (bitwise-reproducible results).  A
     // variant forced with VIE_P3_VARIANT bypasses the cache both ways.
-    const long long key = ((long long)P->n * 2 + (sizeof(T) == 8 ? 0 : 1)) * 8 + K.mode;
+    const long long key = ((long long)P->n * 4 + Prec<T>::id) * 8 + K.mode;
     const bool forced = getenv("VIE_P3_VARIANT") != nullptr;
     if (!forced) {
       std::lock_guard<std::mutex> g(tune_mutex());
@@ -357,7 +359,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
       if (it != tune_cache().end()) p3v = it->second;
     }
     if (p3v < 0) {
-      vie_status e = tune_dispatch(P, K, B, C, sizeof(T) == 8, st, &p3v);
+      vie_status e = tune_dispatch(P, K, B, C, Prec<T>::id, st, &p3v);
       if (e != VIE_OK) return e;
       if (!forced) {
         std::lock_guard<std::mutex> g(tune_mutex());
@@ -369,7 +371,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   if (p3v == kP3Generic) fs.p3 = false;
   // P1
   if (fs.p1) {
-    vie_status e = fast_dispatch(1, P, K, in, out, nrhs, with_identity, A, B, C, sizeof(T) == 8, st);
+    vie_status e = fast_dispatch(1, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[1], st));
   } else {
@@ -377,15 +379,15 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     const size_t smem = vs * (M + 2 * nl * (M + 1));
     VIE_CK(allow_smem(k_p1<T>));
     dim3 grid((n * n + nl - 1) / nl, cin, nrhs);
-    k_p1<T><<<grid, blk, smem, st>>>((const V*)in, A, n, pl, tw, nl, C);
+    k_p1<T><<<grid, blk, smem, st>>>((const typename IOT<T>::E*)in, A, n, pl, tw, nl, C);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[1], st));
   }
-  const int nly = pow2_divisor(M, sizeof(T) == 8 ? 8 : 16);
+  const int nly = pow2_divisor(M, sizeof(V) == 16 ? 8 : 16);
   const size_t smem_y = vs * (M + 2 * nly * (M + 1));
   // P2
   if (fs.py) {
-    vie_status e = fast_dispatch(2, P, K, in, out, nrhs, with_identity, A, B, C, sizeof(T) == 8, st);
+    vie_status e = fast_dispatch(2, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[2], st));
   } else {
@@ -397,7 +399,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   }
   // P3
   if (fs.p3) {
-    vie_status e = fast_dispatch(3, P, K, in, out, nrhs, with_identity, A, B, C, sizeof(T) == 8, st);
+    vie_status e = fast_dispatch(3, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[3], st));
   } else {
@@ -412,7 +414,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   }
   // P4
   if (fs.py) {
-    vie_status e = fast_dispatch(4, P, K, in, out, nrhs, with_identity, A, B, C, sizeof(T) == 8, st);
+    vie_status e = fast_dispatch(4, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[4], st));
   } else {
@@ -424,7 +426,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   }
   // P5
   if (fs.p5) {
-    vie_status e = fast_dispatch(5, P, K, in, out, nrhs, with_identity, A, B, C, sizeof(T) == 8, st);
+    vie_status e = fast_dispatch(5, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[5], st));
   } else {
@@ -433,9 +435,10 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     const size_t smem = vs * (M + 2 * cout * nr * (M + 1));
     VIE_CK(allow_smem(k_p5<T>));
     dim3 grid((n * n + nr - 1) / nr, nrhs);
-    const V* He = Prec<T>::H(P->He64, P->He32);
-    const V* Hm = P->has_mu ? Prec<T>::H(P->Hm64, P->Hm32) : nullptr;
-    k_p5<T><<<grid, blk, smem, st>>>(A, (const V*)in, (V*)out, n, pl, tw, nr, C, cout, He, Hm,
+    const V* He = Prec<T>::He(P);
+    const V* Hm = P->has_mu ? Prec<T>::Hm(P) : nullptr;
+    k_p5<T><<<grid, blk, smem, st>>>(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, pl, tw, nr, C,
+                                     cout, He, Hm,
                                      with_identity ? 1 : 0);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[5], st));
@@ -445,20 +448,20 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
 
 vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant, cudaStream_t st) {
   const int M = 2 * P->n;
-  if (!fast_select(M, K.mode, true).p3) {
+  if (prec == VIE_DF64 || !fast_select(M, K.mode, true).p3) {  // generic kernels: nothing to tune
     *variant = -1;
     return VIE_OK;
   }
-  int& v = P->p3_variant[prec == VIE_FP64 ? 0 : 1][K.mode];
+  int& v = P->p3_variant[prec][K.mode];
   v = -1;
   {
     std::lock_guard<std::mutex> g(tune_mutex());
-    tune_cache().erase(((long long)P->n * 2 + (prec == VIE_FP64 ? 0 : 1)) * 8 + K.mode);
+    tune_cache().erase(((long long)P->n * 4 + prec) * 8 + K.mode);
   }
   // an apply of a zero vector allocates the workspace and tunes on its first call
   const long long L = (long long)cin_of(K.mode) * P->n * P->n * P->n;
   void *x = nullptr, *y = nullptr;
-  const size_t esz = prec == VIE_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t esz = prec == VIE_FP32 ? sizeof(float2) : sizeof(double2);
   VIE_CK(dalloc(&x, esz * L, st));
   VIE_CK(dalloc(&y, esz * (size_t)cout_of(K.mode) * P->n * P->n * P->n, st));
   VIE_CK(cudaMemsetAsync(x, 0, esz * L, st));
@@ -473,6 +476,16 @@ vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
                      bool with_identity, cudaStream_t st) {
   if (prec == VIE_FP64) return run_apply_t<double>(P, K, in, out, nrhs, with_identity, st);
+  if (prec == VIE_DF64) {
+    // double-word tables exist for the operator kernels only
+    if (&K != &P->kapply) {
+      set_error("double-word arithmetic is available for the operator apply only");
+      return VIE_EINVAL;
+    }
+    vie_status s = build_df(P, st);
+    if (s != VIE_OK) return s;
+    return run_apply_t<df>(P, K, in, out, nrhs, with_identity, st);
+  }
   return run_apply_t<float>(P, K, in, out, nrhs, with_identity, st);
 }
 

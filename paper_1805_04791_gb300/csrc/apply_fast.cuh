@@ -12,16 +12,28 @@
 
 namespace vie {
 
+// Per compute type: its precision id (vie_precision) and the device tables it uses.
 template <typename T> struct Prec;
 template <> struct Prec<double> {
+  static constexpr int id = VIE_FP64;
   static const double2* K(const KernelSet& k) { return k.oct64; }
-  static const double2* H(const double2* h64, const float2*) { return h64; }
+  static const double2* He(const vie_problem* P) { return P->He64; }
+  static const double2* Hm(const vie_problem* P) { return P->Hm64; }
   static const double2* tw(const vie_problem* P) { return P->tw64; }
 };
 template <> struct Prec<float> {
+  static constexpr int id = VIE_FP32;
   static const float2* K(const KernelSet& k) { return k.oct32; }
-  static const float2* H(const double2*, const float2* h32) { return h32; }
+  static const float2* He(const vie_problem* P) { return P->He32; }
+  static const float2* Hm(const vie_problem* P) { return P->Hm32; }
   static const float2* tw(const vie_problem* P) { return P->tw32; }
+};
+template <> struct Prec<df> {
+  static constexpr int id = VIE_DF64;
+  static const cdf* K(const KernelSet& k) { return k.octdf; }
+  static const cdf* He(const vie_problem* P) { return P->Hedf; }
+  static const cdf* Hm(const vie_problem* P) { return P->Hmdf; }
+  static const cdf* tw(const vie_problem* P) { return P->twdf; }
 };
 
 template <typename V>
@@ -64,7 +76,7 @@ __device__ __forceinline__ void slab_async(E* slab, const E* src, int narr, int 
 // kx) put consecutive kx on consecutive lanes.  Every global access is a
 // full 128-byte (FP32) or 256-byte (FP64) segment per half-warp.
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) f_p1(const typename CT<T>::V* __restrict__ x, typename CT<T>::V* __restrict__ A,
+__global__ void __launch_bounds__(256) f_p1(const typename IOT<T>::E* __restrict__ x, typename CT<T>::V* __restrict__ A,
                                             int n, int C, const typename CT<T>::V* __restrict__ twg) {
   typedef Fft2<T, R1, R2> F;
   typedef typename CT<T>::V V;
@@ -78,10 +90,10 @@ __global__ void __launch_bounds__(256) f_p1(const typename CT<T>::V* __restrict_
   const int row = blockIdx.x * L + l;
   const bool ok = row < rows;
   const int c = blockIdx.y, b = blockIdx.z, nc = gridDim.y;
-  const V* src = x + ((long long)b * nc + c) * ((long long)rows * n) + (long long)row * n;
+  const typename IOT<T>::E* src = x + ((long long)b * nc + c) * ((long long)rows * n) + (long long)row * n;
   V u[R1];
 #pragma unroll
-  for (int n1 = 0; n1 < R1; ++n1) u[n1] = (n1 < R1 / 2 && ok) ? src[R2 * n1 + t] : CT<T>::make(0, 0);
+  for (int n1 = 0; n1 < R1; ++n1) u[n1] = (n1 < R1 / 2 && ok) ? to_v<T>(src[R2 * n1 + t]) : CT<T>::make(0, 0);
   __syncthreads();
   V* s = sm + l * F::LS;
   F::template fwd1<true>(u, t, s, tw);
@@ -396,8 +408,8 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
             const T sgn = fz ? sg1[i] : sg0[i];
             const T px = kv.x * xv.x - kv.y * xv.y;
             const T py = kv.x * xv.y + kv.y * xv.x;
-            ax = fma(sgn, px, ax);
-            ay = fma(sgn, py, ay);
+            ax = fmadd(sgn, px, ax);
+            ay = fmadd(sgn, py, ay);
           }
           X[j][k2] = CT<T>::make(ax, ay);
         }
@@ -727,7 +739,7 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
 // y = u).  CO = 3 (one H block) or 6 ([J; M] with H_eps and H_mu, or [E; H]).
 template <typename T, int R1, int R2, int CO>
 __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict__ A,
-                                            const typename CT<T>::V* __restrict__ xin, typename CT<T>::V* __restrict__ y,
+                                            const typename IOT<T>::E* __restrict__ xin, typename IOT<T>::E* __restrict__ y,
                                             int n, int C, int cout, const typename CT<T>::V* __restrict__ He,
                                             const typename CT<T>::V* __restrict__ Hm, int with_identity,
                                             const typename CT<T>::V* __restrict__ twg) {
@@ -776,17 +788,17 @@ __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict_
         const V* H = blk == 0 ? He : Hm;
         const V hxx = H[pt], hyy = H[N + pt], hzz = H[2 * N + pt];
         const V hxy = H[3 * N + pt], hxz = H[4 * N + pt], hyz = H[5 * N + pt];
-        const V* xi = xin + ((long long)b * CO + 3 * blk) * N + pt;
-        V* yo = y + ((long long)b * CO + 3 * blk) * N + pt;
+        const typename IOT<T>::E* xi = xin + ((long long)b * CO + 3 * blk) * N + pt;
+        typename IOT<T>::E* yo = y + ((long long)b * CO + 3 * blk) * N + pt;
         const V a0 = uo[3 * blk][n1], a1 = uo[3 * blk + 1][n1], a2 = uo[3 * blk + 2][n1];
-        yo[0] = xi[0] + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2);
-        yo[N] = xi[N] + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2);
-        yo[2 * N] = xi[2 * N] + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2);
+        yo[0] = from_v<T>(to_v<T>(xi[0]) + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
+        yo[N] = from_v<T>(to_v<T>(xi[N]) + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
+        yo[2 * N] = from_v<T>(to_v<T>(xi[2 * N]) + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
       }
     } else {
 #pragma unroll
       for (int c = 0; c < CO; ++c)
-        if (c < cout) y[((long long)b * cout + c) * N + pt] = uo[c][n1];
+        if (c < cout) y[((long long)b * cout + c) * N + pt] = from_v<T>(uo[c][n1]);
     }
   }
 }
@@ -800,7 +812,8 @@ struct FastPath {
   typedef Fft2<f32x2, R1, R2> F2;
   static constexpr int M = R1 * R2, L = 256 / R2;
   static size_t smem() { return sizeof(V) * (M + L * Fft2<T, R1, R2>::LS); }
-  static vie_status p1(const V* x, V* A, int n, int C, int cin, int nrhs, const V* tw, cudaStream_t st) {
+  typedef typename IOT<T>::E E;
+  static vie_status p1(const E* x, V* A, int n, int C, int cin, int nrhs, const V* tw, cudaStream_t st) {
     VIE_CK(allow_smem(f_p1<T, R1, R2>));
     f_p1<T, R1, R2><<<dim3((n * n + L - 1) / L, cin, nrhs), 256, smem(), st>>>(x, A, n, C, tw);
     VIE_CK(cudaGetLastError());
@@ -942,7 +955,7 @@ struct FastPath {
       default: return p3_mode<KM_MAXWELL6>(variant, B, n, C, K, nrhs, tw, done, st);
     }
   }
-  static vie_status p5(const V* A, const V* xin, V* y, int n, int C, int cout, const V* He, const V* Hm, bool wid,
+  static vie_status p5(const V* A, const E* xin, E* y, int n, int C, int cout, const V* He, const V* Hm, bool wid,
                        int nrhs, const V* tw, cudaStream_t st) {
     const dim3 grid((n * n + L - 1) / L, nrhs);
     if (cout <= 3) {
@@ -966,11 +979,11 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
   const V* tw = Prec<T>::tw(P);
   const int cin = cin_of(K.mode), cout = cout_of(K.mode);
   switch (pass) {
-    case 1: return FP::p1((const V*)in, A, n, C, cin, nrhs, tw, st);
+    case 1: return FP::p1((const typename IOT<T>::E*)in, A, n, C, cin, nrhs, tw, st);
     case 2: return FP::template py<-1>(A, B, n, C, cin, nrhs, tw, st);
     case 3: {
       bool done = false;
-      vie_status e = FP::p3v(P->p3_variant[sizeof(T) == 8 ? 0 : 1][K.mode], B, n, C, Prec<T>::K(K), K.mode, nrhs,
+      vie_status e = FP::p3v(P->p3_variant[Prec<T>::id][K.mode], B, n, C, Prec<T>::K(K), K.mode, nrhs,
                              tw, &done, st);
       if (e == VIE_OK && !done) {
         set_error("selected z-pass variant does not apply to this shape");
@@ -980,8 +993,8 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
     }
     case 4: return FP::template py<+1>(B, A, n, C, cout, nrhs, tw, st);
     default:
-      return FP::p5(A, (const V*)in, (V*)out, n, C, cout, Prec<T>::H(P->He64, P->He32),
-                    P->has_mu ? Prec<T>::H(P->Hm64, P->Hm32) : nullptr, with_identity, nrhs, tw, st);
+      return FP::p5(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, C, cout, Prec<T>::He(P),
+                    P->has_mu ? Prec<T>::Hm(P) : nullptr, with_identity, nrhs, tw, st);
   }
 }
 

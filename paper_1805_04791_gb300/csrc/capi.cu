@@ -38,14 +38,17 @@ static bool smooth_size(int n) {
 static void free_set(KernelSet& k, cudaStream_t st) {
   dfree(k.oct64, st);
   dfree(k.oct32, st);
+  dfree(k.octdf, st);
   k.oct64 = nullptr;
   k.oct32 = nullptr;
+  k.octdf = nullptr;
 }
 
 static void free_problem(vie_problem* P) {
   if (!P) return;
   cudaStream_t st = P->stream;
-  void* ptrs[] = {P->tw64, P->tw32, P->He64, P->He32, P->Hm64, P->Hm32, P->sym_oct, P->ws.buf, P->ks.buf, P->dflag};
+  void* ptrs[] = {P->tw64, P->tw32, P->He64, P->He32, P->Hm64, P->Hm32, P->twdf, P->Hedf, P->Hmdf,
+                  P->sym_oct, P->ws.buf, P->ks.buf, P->dflag};
   for (void* q : ptrs) dfree(q, st);
   free_set(P->kapply, st);
   free_set(P->keval, st);
@@ -134,7 +137,7 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
 int vie_problem_ncomp(const vie_problem* P) { return P ? P->ncomp : 0; }
 
 vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream) {
-  if (!P || !x || !y || nrhs < 1 || (precision != VIE_FP64 && precision != VIE_FP32)) {
+  if (!P || !x || !y || nrhs < 1 || (precision != VIE_FP64 && precision != VIE_FP32 && precision != VIE_DF64)) {
     set_error("vie_apply: bad argument");
     return VIE_EINVAL;
   }
@@ -185,6 +188,7 @@ size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu) {
   size_t held = 144 * N * (has_mu ? 2 : 1);  // H: 6 entries, FP64 + FP32
   held += 16 * O3 * nsym;                    // raw symbol octants
   held += 24 * O3 * 18;                      // apply + eval kernel sets, FP64 + FP32
+  held += 96 * N * (has_mu ? 2 : 1) + 16 * O3 * (kind == VIE_MAXWELL ? 9 : 6);  // double-word copies (mixed solve)
   // set-up peak: oversampled (3n)^3 and (2n)^3 FP64 transform buffers
   const size_t setup = held + 16 * (27 * N + 8 * N);
   // steady state: FP64 apply workspace, mixed-precision Krylov group
@@ -194,7 +198,7 @@ size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu) {
 }
 
 vie_status vie_tune(vie_problem* P, int precision, int* variant, void* stream) {
-  if (!P || !variant || (precision != VIE_FP64 && precision != VIE_FP32)) {
+  if (!P || !variant || (precision != VIE_FP64 && precision != VIE_FP32 && precision != VIE_DF64)) {
     set_error("vie_tune: bad argument");
     return VIE_EINVAL;
   }

@@ -13,6 +13,7 @@
 // norm.  Reductions use a fixed order (reruns are bit-identical); per-thread
 // partial sums are FP64 for an FP64 basis and FP32 for an FP32 basis, the
 // cross-thread sums always FP64.
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -698,6 +699,11 @@ static vie_status run_bicgstab(vie_problem* P, const void* rhs, void* Jv, const 
   return VIE_OK;
 }
 
+static bool residual_fp64() {
+  const char* e = getenv("VIE_RESIDUAL_FP64");
+  return e && e[0] == '1';
+}
+
 vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_opts* opt, vie_solve_info* info,
                      cudaStream_t st) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -756,7 +762,9 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
         VIE_CK(cudaMemcpyAsync(g.r, b, sizeof(double2) * nb * L, cudaMemcpyDeviceToDevice, st));
         beta = nbv;
       } else {
-        s = run_apply(P, P->kapply, x, g.r, VIE_FP64, nb, true, st);
+        // mixed: the residual in double-word arithmetic (FP64 accuracy, FP32
+        // pipes); VIE_RESIDUAL_FP64=1 takes the native FP64 apply instead
+        s = run_apply(P, P->kapply, x, g.r, (mixed && !residual_fp64()) ? VIE_DF64 : VIE_FP64, nb, true, st);
         if (s != VIE_OK) return s;
         inf.applies_fp64 += nb;
         k_bminus<<<ew_blocks(L * nb), 256, 0, st>>>(g.r, b, L * nb);
@@ -776,7 +784,9 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
         if (!conv[r]) all = false;
         // converged members ride along with zero vectors
         bx[r] = conv[r] ? 0.0 : beta[r];
-        stop[r] = mixed ? opt->inner_tol * beta[r] : 0.5 * opt->tol * nbv[r];
+        // mixed: an inner solve need not go below what the overall target
+        // requires; the 0.25 leaves room for the FP32 operator's own error
+        stop[r] = mixed ? std::max(opt->inner_tol * beta[r], 0.25 * opt->tol * nbv[r]) : 0.5 * opt->tol * nbv[r];
       }
       if (all || outer == max_outer || total_inner >= opt->max_inner) break;
       std::vector<int> steps;

@@ -6,6 +6,7 @@
 //  * the discrete kernels of every Fourier symbol (1, i k_a, -k_a k_b) with the
 //    grid Nyquist cutoff (Sec. 5, step c), brought to the (2n)^3 convolution
 //    grid and stored as octants (the kernels are even or odd in each axis).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -463,6 +464,37 @@ static vie_status combine_sets(vie_problem* P, int which, cudaStream_t st) {
   }
   VIE_CK(cudaStreamSynchronize(st));
   return VIE_OK;
+}
+
+// ------------------------------------------------------------ double-word copies
+// v -> (hi, lo) with hi = fl32(v), lo = fl32(v - hi): the double-word value
+// equals v to about 2^-48 relative.
+__global__ void k_to_df(const double2* __restrict__ src, cdf* __restrict__ dst, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    dst[i] = CT<df>::make(df(v.x), df(v.y));
+  }
+}
+
+static vie_status to_df(const double2* src, cdf** dst, long long count, cudaStream_t st) {
+  VIE_CK(dalloc((void**)dst, sizeof(cdf) * (size_t)count, st));
+  const long long blocks = std::min<long long>((count + 255) / 256, 4096);
+  k_to_df<<<(unsigned)blocks, 256, 0, st>>>(src, *dst, count);
+  VIE_CK(cudaGetLastError());
+  return VIE_OK;
+}
+
+vie_status build_df(vie_problem* P, cudaStream_t st) {
+  if (P->kapply.octdf) return VIE_OK;
+  const long long N = (long long)P->n * P->n * P->n;
+  const long long O3 = (long long)(P->n + 1) * (P->n + 1) * (P->n + 1);
+  vie_status s = VIE_OK;
+  if (!P->twdf) s = to_df(P->tw64, &P->twdf, 2 * P->n, st);
+  if (s == VIE_OK && !P->Hedf) s = to_df(P->He64, &P->Hedf, 6 * N, st);
+  if (s == VIE_OK && P->Hm64 && !P->Hmdf) s = to_df(P->Hm64, &P->Hmdf, 6 * N, st);
+  if (s == VIE_OK) s = to_df(P->kapply.oct64, &P->kapply.octdf, (long long)P->kapply.narr * O3, st);
+  return s;
 }
 
 }  // namespace vie

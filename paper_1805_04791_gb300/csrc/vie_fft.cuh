@@ -124,6 +124,85 @@ __device__ __forceinline__ c32x2 cmulc(c32x2 a, c32x2 b) {
   return CT<f32x2>::make(fmadd(a.x, b.x, a.y * b.y), fmadd(a.y, b.x, -(a.x * b.y)));
 }
 
+// ------------------------------------------------ double-word arithmetic
+// df holds a real number as the unevaluated sum hi + lo of two FP32 values
+// with |lo| <= ulp(hi)/2, about 48 significant bits.  The operations are the
+// double-word algorithms of Joldes, Muller and Popescu (ACM TOMS 44(2), 2017):
+// addition "AccurateDWPlusDW" (relative error <= 3u^2) and multiplication
+// "DWTimesDW3" (<= 4u^2, with FMA), built on Knuth's TwoSum, Dekker's
+// Fast2Sum and the FMA-exact product, u = 2^-24.  Every step is an explicitly
+// rounded intrinsic, so compiler contraction cannot alter the error-free
+// transformations.  All of it runs on the FP32 pipes, which on this GPU have
+// 64 times the FP64 throughput.
+struct __align__(8) df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+struct __align__(16) cdf {
+  df x, y;
+};
+template <> struct CT<df> {
+  typedef cdf V;
+  static __host__ __device__ __forceinline__ V make(df a, df b) {
+    V r;
+    r.x = a;
+    r.y = b;
+    return r;
+  }
+};
+// s + e = a + b exactly (TwoSum)
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// s + e = a + b exactly when the exponent of a is not below that of b (Fast2Sum)
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df operator+(df x, df y) {
+  const df s = two_sum(x.hi, y.hi), t = two_sum(x.lo, y.lo);
+  const df v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ df operator-(df x) { return df(-x.hi, -x.lo); }
+__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
+__device__ __forceinline__ df operator*(df x, df y) {
+  const float ch = __fmul_rn(x.hi, y.hi);
+  const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+  const float tl1 = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.lo));
+  const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+__device__ __forceinline__ df fmadd(df a, df b, df c) { return a * b + c; }
+__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return CT<df>::make(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return CT<df>::make(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cdf operator*(df s, cdf a) { return CT<df>::make(s * a.x, s * a.y); }
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) {
+  return CT<df>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ cdf cmulc(cdf a, cdf b) {
+  return CT<df>::make(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// Element type a compute type reads and writes at the operator's interface
+// (the FP64 vectors x, y for the double-word path), and the conversions.
+template <typename T> struct IOT { typedef typename CT<T>::V E; };
+template <> struct IOT<df> { typedef double2 E; };
+template <typename T>
+__device__ __forceinline__ typename CT<T>::V to_v(typename IOT<T>::E e) { return e; }
+template <>
+__device__ __forceinline__ cdf to_v<df>(double2 e) { return CT<df>::make(df(e.x), df(e.y)); }
+template <typename T>
+__device__ __forceinline__ typename IOT<T>::E from_v(typename CT<T>::V v) { return v; }
+template <>
+__device__ __forceinline__ double2 from_v<df>(cdf v) {
+  return make_double2((double)v.x.hi + (double)v.x.lo, (double)v.y.hi + (double)v.y.lo);
+}
+
 // a * (S i) for S = +1 / -1
 template <int S, typename V>
 __device__ __forceinline__ V mul_si(V a) {

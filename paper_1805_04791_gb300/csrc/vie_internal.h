@@ -44,6 +44,7 @@ struct KernelSet {
   int narr = 0;                 // 3, 6 or 9
   double2* oct64 = nullptr;     // [narr][(n+1)^3] FP64
   float2* oct32 = nullptr;      // [narr][(n+1)^3] FP32
+  cdf* octdf = nullptr;         // [narr][(n+1)^3] double-word (built on first VIE_DF64 apply)
 };
 
 struct Workspace {
@@ -77,6 +78,9 @@ struct vie_problem {
   float2* He32 = nullptr;
   double2* Hm64 = nullptr;   // [6][n^3] H_mu (Maxwell with mu)
   float2* Hm32 = nullptr;
+  vie::cdf* twdf = nullptr;  // double-word copies of tw64, He64, Hm64 (first VIE_DF64 apply)
+  vie::cdf* Hedf = nullptr;
+  vie::cdf* Hmdf = nullptr;
   double2* sym_oct = nullptr;  // [SYM_COUNT][(n+1)^3] raw symbol kernels DFT_{2n}, FP64
   unsigned sym_mask = 0;       // symbols computed so far
   vie::KernelSet kapply;     // operator kernels (with I/2, 2H sign and 1/(2n)^3 folded in)
@@ -84,7 +88,7 @@ struct vie_problem {
   vie::Workspace ws;         // padded intermediates
   vie::Workspace ks;         // Krylov workspace
   vie::Profiler prof;
-  int p3_variant[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};  // tuned z-pass variant per (precision, mode)
+  int p3_variant[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // tuned z-pass variant per (precision, mode)
   int* dflag = nullptr;      // device error flag (NaN, bad input)
 };
 
@@ -108,9 +112,11 @@ vie_status build_medium(vie_problem* P, const void* eps, const void* mu, cudaStr
 vie_status build_kernels(vie_problem* P, cudaStream_t st);
 vie_status build_eval_kernels(vie_problem* P, cudaStream_t st);
 vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st);
+// Double-word copies of the twiddles, medium tensors and apply kernels (idempotent).
+vie_status build_df(vie_problem* P, cudaStream_t st);
 
 // apply.cu
-// Convolution pipeline: out = epilogue(K * pad(in)).  prec 0 = FP64, 1 = FP32.
+// Convolution pipeline: out = epilogue(K * pad(in)).  prec: vie_precision.
 // in/out layout [nrhs][c][n][n][n] complex.  If with_identity, out = in + H u
 // (u = the convolution); otherwise out = u.
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
