@@ -196,7 +196,9 @@ vie_status vie_problem_destroy(vie_problem* P);
  * component per thread; 3 one CTA per tile of 8 pencils; 4/5/6 (FP32 only,
  * 2n in {64, 96, 128, 256}) as 0/1/2 with two neighbouring pencils per
  * thread packed as f32x2 lanes; 7/8/9 (FP32 only, same sizes) mirror-group
- * CTAs of 8/4/16 pencils with all three components of a vector per thread.
+ * CTAs of 8/4/16 pencils with all three components of a vector per thread;
+ * 10/11 as 7/8 with a grid sized to the device, each CTA walking several
+ * mirror groups and prefetching the next one's inputs and kernel values.
  * vie_apply
  * tunes on its first call for a precision anyway; calling vie_tune first keeps
  * the tuning time out of a timed or captured region.  Synchronises the stream.

@@ -102,8 +102,7 @@ __device__ __forceinline__ V kval(const V* __restrict__ K, int a, long long O3, 
   if (ky > n) { oy = M - ky; if (par & 2) sgn = -sgn; }
   if (kx > n) { ox = M - kx; if (par & 1) sgn = -sgn; }
   V v = K[a * O3 + ((long long)oz * O + oy) * O + ox];
-  if (sgn < 0) { v.x = -v.x; v.y = -v.y; }
-  return v;
+  return (sgn < 0) ? vneg(v) : v;
 }
 
 template <typename T>
@@ -163,9 +162,9 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
         const V pxj1 = cmul(p[2], u[0]) - cmul(p[0], u[2]);
         const V pxj2 = cmul(p[0], u[1]) - cmul(p[1], u[0]);
         if (mode == KM_EMRED) {
-          o[3] = CT<T>::make(-pxj0.x, -pxj0.y);
-          o[4] = CT<T>::make(-pxj1.x, -pxj1.y);
-          o[5] = CT<T>::make(-pxj2.x, -pxj2.y);
+          o[3] = vneg(pxj0);
+          o[4] = vneg(pxj1);
+          o[5] = vneg(pxj2);
         } else {
           // u[3..5] = M: Q M - P x J ; and add P x M to the J rows
           o[3] = cmul(qxx, u[3]) + cmul(qxy, u[4]) + cmul(qxz, u[5]) - pxj0;
@@ -253,6 +252,21 @@ static dim3 line_block(int M) {
   return dim3(tx, 256 / tx);
 }
 
+// Lines per CTA of a one-component generic pass: as many as a 256-thread block
+// holds (one thread row per line), with the tile kept near 72 KB of shared
+// memory so that three CTAs share an SM also for 16-byte elements.
+static int lines_for(int M, size_t vs) {
+  const int cap = 256 / (int)line_block(M).x;
+  int nl = pow2_divisor(M, cap);
+  while (nl > 1 && vs * (M + 2 * (size_t)nl * (M + 1)) > 72 * 1024) nl >>= 1;
+  return nl;
+}
+// Block of a generic pass over `lines` lines: no thread row left idle.
+static dim3 block_for(int M, int lines) {
+  const dim3 b = line_block(M);
+  return dim3(b.x, std::max(1, std::min((int)b.y, lines)));
+}
+
 size_t apply_workspace_bytes(int n, int c, int nrhs, int prec) {
   const size_t esz = prec == VIE_FP32 ? sizeof(float2) : sizeof(double2);  // double-word complex is 16 bytes too
   const size_t M = 2 * (size_t)n;
@@ -333,7 +347,6 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   const V* tw = Prec<T>::tw(P);
   const V* Kp = Prec<T>::K(K);
   const FftPlan& pl = P->plan2n;
-  const dim3 blk = line_block(M);
   const size_t vs = sizeof(V);
   Profiler& pf = P->prof;
   const bool rec = pf.on && pf.count < pf.cap;
@@ -375,15 +388,15 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[1], st));
   } else {
-    const int nl = (int)blk.y;
+    const int nl = lines_for(M, vs);
     const size_t smem = vs * (M + 2 * nl * (M + 1));
     VIE_CK(allow_smem(k_p1<T>));
     dim3 grid((n * n + nl - 1) / nl, cin, nrhs);
-    k_p1<T><<<grid, blk, smem, st>>>((const typename IOT<T>::E*)in, A, n, pl, tw, nl, C);
+    k_p1<T><<<grid, block_for(M, nl), smem, st>>>((const typename IOT<T>::E*)in, A, n, pl, tw, nl, C);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[1], st));
   }
-  const int nly = pow2_divisor(M, sizeof(V) == 16 ? 8 : 16);
+  const int nly = lines_for(M, vs);
   const size_t smem_y = vs * (M + 2 * nly * (M + 1));
   // P2
   if (fs.py) {
@@ -393,7 +406,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   } else {
     VIE_CK(allow_smem(k_py<T, -1>));
     dim3 grid(M / nly, n, nrhs * cin);
-    k_py<T, -1><<<grid, blk, smem_y, st>>>(A, B, n, pl, tw, nly, C, cin);
+    k_py<T, -1><<<grid, block_for(M, nly), smem_y, st>>>(A, B, n, pl, tw, nly, C, cin);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[2], st));
   }
@@ -408,7 +421,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     const size_t smem = vs * (M + 2 * C * nl * (M + 1));
     VIE_CK(allow_smem(k_p3<T>));
     dim3 grid(M / nl, M, nrhs);
-    k_p3<T><<<grid, blk, smem, st>>>(B, n, pl, tw, nl, C, Kp, K.mode);
+    k_p3<T><<<grid, block_for(M, C * nl), smem, st>>>(B, n, pl, tw, nl, C, Kp, K.mode);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[3], st));
   }
@@ -420,7 +433,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   } else {
     VIE_CK(allow_smem(k_py<T, +1>));
     dim3 grid(M / nly, n, nrhs * cout);
-    k_py<T, +1><<<grid, blk, smem_y, st>>>(B, A, n, pl, tw, nly, C, cout);
+    k_py<T, +1><<<grid, block_for(M, nly), smem_y, st>>>(B, A, n, pl, tw, nly, C, cout);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[4], st));
   }
@@ -437,7 +450,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     dim3 grid((n * n + nr - 1) / nr, nrhs);
     const V* He = Prec<T>::He(P);
     const V* Hm = P->has_mu ? Prec<T>::Hm(P) : nullptr;
-    k_p5<T><<<grid, blk, smem, st>>>(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, pl, tw, nr, C,
+    k_p5<T><<<grid, block_for(M, cout * nr), smem, st>>>(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, pl, tw, nr, C,
                                      cout, He, Hm,
                                      with_identity ? 1 : 0);
     VIE_CK(cudaGetLastError());

@@ -588,6 +588,7 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
   constexpr int GO = (MODE == KM_DIV) ? 1 : 3;  // output components per thread
   constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
   constexpr int M = F::M, NTX = M / NP, NTHR = NP * R2 * NG, H = R1 / 2;
+  constexpr int NGROUPS = (M / 2 + 1) * (NTX / 2);  // mirror groups
   constexpr int LS = ((F::LS0 + 13) / 16) * 16 + 2;
   constexpr int QW = NP + 1;
   static_assert(MODE == KM_SYM3 || MODE == KM_DIV || MODE == KM_MAXWELL6, "component-group z pass");
@@ -595,38 +596,57 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
   V* tw = (V*)smraw;
   V* sm = tw + M;
   V* slab = sm + NG * G * NP * LS;
-  const int kyp = blockIdx.x / (NTX / 2), txp = blockIdx.x - (blockIdx.x / (NTX / 2)) * (NTX / 2);
   const int O = n + 1, OP = ((O + 13) / 16) * 16 + 2;
   const long long O3 = (long long)O * O * O;
-  {
-    // kernel slab [a][q][oz] <- K[a][oz][kyp][NP txp + q], in flight during tile 0's forward transforms
-    const V* src = K + (long long)kyp * O + NP * txp;
+  const int l = threadIdx.x % NP, t = (threadIdx.x / NP) % R2, h = threadIdx.x / (NP * R2);
+  const long long zs = (long long)M * M, cs = (long long)n * zs;
+  const int b0 = blockIdx.y;
+  // The CTA walks mirror groups blockIdx.x, blockIdx.x + gridDim.x, ... (a single
+  // group when the grid has one CTA per group).  Group grp = (kyp, txp) owns the tiles
+  // (ky, M - ky) x (kx tile, mirrored tile); rows ky = 0 and M/2 mirror onto themselves.
+  auto g_kyp = [&](int grp) { return grp / (NTX / 2); };
+  auto g_txp = [&](int grp) { return grp - (grp / (NTX / 2)) * (NTX / 2); };
+  auto g_self = [&](int grp) {
+    const int k = grp / (NTX / 2);
+    return k == 0 || k == M / 2;
+  };
+  auto tile_ky = [&](int grp, int i) {
+    const int v = g_self(grp) ? 2 * i : i;
+    return (v & 1) ? M - g_kyp(grp) : g_kyp(grp);
+  };
+  auto tile_kx = [&](int grp, int i) {
+    const int v = g_self(grp) ? 2 * i : i;
+    return ((v & 2) ? NTX - 1 - g_txp(grp) : g_txp(grp)) * NP + l;
+  };
+  // kernel slab [a][q][oz] <- K[a][oz][kyp][NP txp + q], copied while other work runs
+  auto slab_issue = [&](int grp) {
+    const V* src = K + (long long)g_kyp(grp) * O + NP * g_txp(grp);
     for (int a = 0; a < NARR; ++a)
       for (int idx = threadIdx.x; idx < O * QW; idx += NTHR) {
         const int oz = idx / QW, q = idx - oz * QW;
         cp_async<8>(slab + (a * QW + q) * OP + oz, src + a * O3 + (long long)oz * O * O + q);
       }
     cp_async_commit();
-  }
-  for (int j = threadIdx.x; j < M; j += NTHR) tw[j] = twg[j];
-  const int l = threadIdx.x % NP, t = (threadIdx.x / NP) % R2, h = threadIdx.x / (NP * R2);
-  const long long zs = (long long)M * M, cs = (long long)n * zs;
-  const int b0 = blockIdx.y;
-  const bool self_y = (kyp == 0 || kyp == M / 2);
-  const int ntiles = self_y ? 2 : 4;  // mirror tiles (ky, M - ky) x (kx tile, mirrored tile)
-  auto tile_ky = [&](int i) { const int v = self_y ? 2 * i : i; return (v & 1) ? M - kyp : kyp; };
-  auto tile_kx = [&](int i) { const int v = self_y ? 2 * i : i; return ((v & 2) ? NTX - 1 - txp : txp) * NP + l; };
-  V g[G][H];  // this (then the next) tile's inputs, z < n
-  {
-    const V* src = B + (long long)b0 * C * cs + (long long)tile_ky(0) * M + tile_kx(0) + (long long)(h * G) * cs;
+  };
+  V g[G][H];  // inputs (z < n) of the tile being started, then of the next one
+  auto load_inputs = [&](int grp, int i) {
+    const V* src =
+        B + (long long)b0 * C * cs + (long long)tile_ky(grp, i) * M + tile_kx(grp, i) + (long long)(h * G) * cs;
 #pragma unroll
     for (int c = 0; c < G; ++c)
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) g[c][n1] = src[c * cs + (long long)(R2 * n1 + t) * zs];
-  }
+  };
+  int grp = blockIdx.x;
+  if (grp >= NGROUPS) return;  // block-uniform
+  slab_issue(grp);
+  for (int j = threadIdx.x; j < M; j += NTHR) tw[j] = twg[j];
+  load_inputs(grp, 0);
+  int i = 0;
 #pragma unroll 1
-  for (int i = 0; i < ntiles; ++i) {
-    const int ky = tile_ky(i), kx = tile_kx(i);
+  while (true) {
+    const int ky = tile_ky(grp, i), kx = tile_kx(grp, i);
+    const int txp = g_txp(grp);
     V* colbase = B + (long long)b0 * C * cs + (long long)ky * M + kx;
     V* s0 = sm + ((h * G) * NP + l) * LS;  // this group's transpose lines, component c at s0 + c NP LS
     __syncthreads();                       // previous tile's readers of the transpose lines are done
@@ -642,13 +662,14 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
         F::template fwd1w<true>(u, t, s0 + c * NP * LS, w);
       }
     }
-    if (i + 1 < ntiles) {  // prefetch the next tile
-      const V* src = B + (long long)b0 * C * cs + (long long)tile_ky(i + 1) * M + tile_kx(i + 1) + (long long)(h * G) * cs;
-#pragma unroll
-      for (int c = 0; c < G; ++c)
-#pragma unroll
-        for (int n1 = 0; n1 < H; ++n1) g[c][n1] = src[c * cs + (long long)(R2 * n1 + t) * zs];
+    // the next unit: the next tile of this group, else the first tile of the CTA's next group
+    int ngrp = grp, ni = i + 1;
+    if (ni >= (g_self(grp) ? 2 : 4)) {
+      ngrp = grp + gridDim.x;
+      ni = 0;
     }
+    const bool more = ngrp < NGROUPS;
+    if (more) load_inputs(ngrp, ni);
     __syncthreads();
     V X[G][F::J][R2];
 #pragma unroll
@@ -725,6 +746,8 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
 #pragma unroll
     for (int c = 0; c < GO; ++c) F::invA(X[c], t, s0 + c * NP * LS, tw);
     __syncthreads();
+    // every thread is past this group's mixing: the slab may take the next group's kernel
+    if (more && ni == 0) slab_issue(ngrp);
 #pragma unroll
     for (int c = 0; c < GO; ++c) {
       V u[R1];
@@ -732,6 +755,9 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) colbase[(h * G + c) * cs + (long long)(R2 * n1 + t) * zs] = u[n1];
     }
+    if (!more) break;
+    grp = ngrp;
+    i = ni;
   }
 }
 
@@ -888,7 +914,7 @@ struct FastPath {
       }
     }
   }
-  template <int MODE, int NP>
+  template <int MODE, int NP, bool PERSIST = false>
   static vie_status p3t(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
     *done = false;
     if constexpr (sizeof(T) != 4 || Fft2<T, R1, R2>::J * R2 > 16 || R1 > 16 ||
@@ -908,7 +934,16 @@ struct FastPath {
       } else {
         if (sm > smem_optin()) return VIE_OK;
         VIE_CK(allow_smem(f_p3t<R1, R2, MODE, NP>));
-        f_p3t<R1, R2, MODE, NP><<<dim3((M / 2 + 1) * (NTX / 2), nrhs), NTHR, sm, st>>>(
+        int groups = (M / 2 + 1) * (NTX / 2);
+        if (PERSIST) {  // as many CTAs as fit at once; each walks several mirror groups
+          int dev = 0, sms = 0, per = 0;
+          VIE_CK(cudaGetDevice(&dev));
+          VIE_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+          VIE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f_p3t<R1, R2, MODE, NP>, NTHR, sm));
+          if (per < 1) return VIE_OK;
+          groups = std::min(groups, sms * per);
+        }
+        f_p3t<R1, R2, MODE, NP><<<dim3(groups, nrhs), NTHR, sm, st>>>(
             (float2*)B, n, C, (const float2*)K, (const float2*)tw);
         VIE_CK(cudaGetLastError());
         *done = true;
@@ -942,7 +977,9 @@ struct FastPath {
       case 6: return p3p<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
       case 7: return p3t<MODE, 8>(B, n, C, K, nrhs, tw, done, st);
       case 8: return p3t<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
-      default: return p3t<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
+      case 9: return p3t<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
+      case 10: return p3t<MODE, 8, true>(B, n, C, K, nrhs, tw, done, st);
+      default: return p3t<MODE, 4, true>(B, n, C, K, nrhs, tw, done, st);
     }
   }
   // Run P3 variant `variant` (0..kP3Variants-1); *done = false if it does not apply to this shape.
@@ -1000,13 +1037,14 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
 
 // Autotuner for the z pass: every applicable variant (mirror-group CTAs with
 // 8, 16 or 4 pencils, one tile per CTA with 8 pencils, lane-pair
-// mirror-group CTAs with 8, 16 or 4 pencils, or component-group mirror-group
-// CTAs with 8, 4 or 16 pencils) is launched once
+// mirror-group CTAs with 8, 16 or 4 pencils, component-group mirror-group
+// CTAs with 8, 4 or 16 pencils, or component-group CTAs of 8 or 4 pencils
+// sized to the device, each walking several mirror groups) is launched once
 // to warm up and then timed over 3 launches with CUDA events on the buffer B
 // (whose contents are scratch at this point); the fastest is kept for the
 // problem's (precision, mode).  VIE_TUNE=0 takes the first applicable variant;
 // VIE_P3_VARIANT=k forces variant k.
-static const int kP3Variants = 10;
+static const int kP3Variants = 12;
 static const int kP3Generic = 99;
 
 template <typename T, int R1, int R2>

@@ -140,15 +140,20 @@ struct __align__(8) df {
   __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
   __host__ __device__ constexpr df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
 };
+// A complex double-word number is stored as two lane pairs, h = (re.hi, im.hi)
+// and l = (re.lo, im.lo), so that the real and imaginary parts go through every
+// double-word step together as packed f32x2 instructions (each lane rounded
+// exactly as the scalar algorithm would be); multiplication by +-i is a lane
+// swap.
 struct __align__(16) cdf {
-  df x, y;
+  float2 h, l;
 };
 template <> struct CT<df> {
   typedef cdf V;
-  static __host__ __device__ __forceinline__ V make(df a, df b) {
+  static __host__ __device__ __forceinline__ V make(df re, df im) {
     V r;
-    r.x = a;
-    r.y = b;
+    r.h = make_float2(re.hi, im.hi);
+    r.l = make_float2(re.lo, im.lo);
     return r;
   }
 };
@@ -178,15 +183,91 @@ __device__ __forceinline__ df operator*(df x, df y) {
   return fast_two_sum(ch, __fadd_rn(cl1, cl2));
 }
 __device__ __forceinline__ df fmadd(df a, df b, df c) { return a * b + c; }
-__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return CT<df>::make(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return CT<df>::make(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ cdf operator*(df s, cdf a) { return CT<df>::make(s * a.x, s * a.y); }
+
+// ---- lane-pair building blocks (two independent double-words per operation)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 bcx(float2 a) { return make_float2(a.x, a.x); }
+__device__ __forceinline__ float2 bcy(float2 a) { return make_float2(a.y, a.y); }
+// (h, l) <- Fast2Sum(a, b) and TwoSum(a, b), per lane
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& h, float2& l) {
+  h = add2(a, b);
+  l = sub2(b, sub2(h, a));
+}
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& h, float2& l) {
+  h = add2(a, b);
+  const float2 bb = sub2(h, a);
+  l = add2(sub2(a, sub2(h, bb)), sub2(b, bb));
+}
+// AccurateDWPlusDW per lane: (xh, xl) + (yh, yl)
+__device__ __forceinline__ cdf dw_add2(float2 xh, float2 xl, float2 yh, float2 yl) {
+  float2 sh, sl, th, tl, vh, vl;
+  two_sum2(xh, yh, sh, sl);
+  two_sum2(xl, yl, th, tl);
+  fast_two_sum2(sh, add2(sl, th), vh, vl);
+  cdf r;
+  fast_two_sum2(vh, add2(tl, vl), r.h, r.l);
+  return r;
+}
+// DWTimesDW3 per lane: (xh, xl) (yh, yl)
+__device__ __forceinline__ cdf dw_mul2(float2 xh, float2 xl, float2 yh, float2 yl) {
+  const float2 ch = mul2(xh, yh);
+  const float2 cl1 = fma2(xh, yh, neg2(ch));
+  const float2 tl1 = fma2(xh, yl, mul2(xl, yl));
+  const float2 cl2 = fma2(xl, yh, tl1);
+  cdf r;
+  fast_two_sum2(ch, add2(cl1, cl2), r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return dw_add2(a.h, a.l, b.h, b.l); }
+__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return dw_add2(a.h, a.l, neg2(b.h), neg2(b.l)); }
+__device__ __forceinline__ cdf operator*(df s, cdf a) {
+  return dw_mul2(a.h, a.l, make_float2(s.hi, s.hi), make_float2(s.lo, s.lo));
+}
+// a b = a (bx, bx) + swap(a) (-by, by)
 __device__ __forceinline__ cdf cmul(cdf a, cdf b) {
-  return CT<df>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  const cdf p = dw_mul2(a.h, a.l, bcx(b.h), bcx(b.l));
+  const cdf q = dw_mul2(swp(a.h), swp(a.l), make_float2(-b.h.y, b.h.y), make_float2(-b.l.y, b.l.y));
+  return p + q;
 }
+// a conj(b) = a (bx, bx) + swap(a) (by, -by)
 __device__ __forceinline__ cdf cmulc(cdf a, cdf b) {
-  return CT<df>::make(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+  const cdf p = dw_mul2(a.h, a.l, bcx(b.h), bcx(b.l));
+  const cdf q = dw_mul2(swp(a.h), swp(a.l), make_float2(b.h.y, -b.h.y), make_float2(b.l.y, -b.l.y));
+  return p + q;
 }
+// a (c + i s) = a (c, c) + swap(a) (-s, s)
+__device__ __forceinline__ cdf rot(cdf a, df c, df s) {
+  const cdf p = dw_mul2(a.h, a.l, make_float2(c.hi, c.hi), make_float2(c.lo, c.lo));
+  const cdf q = dw_mul2(swp(a.h), swp(a.l), make_float2(-s.hi, s.hi), make_float2(-s.lo, s.lo));
+  return p + q;
+}
+__device__ __forceinline__ cdf cfma(df s, cdf a, cdf c) { return c + s * a; }
+__device__ __forceinline__ cdf vneg(cdf a) {
+  cdf r;
+  r.h = neg2(a.h);
+  r.l = neg2(a.l);
+  return r;
+}
+// S i a = swap(a) (-S, S)
+template <int S>
+__device__ __forceinline__ cdf mul_si(cdf a) {
+  cdf r;
+  r.h = (S > 0) ? make_float2(-a.h.y, a.h.x) : make_float2(a.h.y, -a.h.x);
+  r.l = (S > 0) ? make_float2(-a.l.y, a.l.x) : make_float2(a.l.y, -a.l.x);
+  return r;
+}
+template <int S>
+__device__ __forceinline__ cdf addi(cdf a, cdf b) {
+  const cdf ib = mul_si<S>(b);
+  return dw_add2(a.h, a.l, ib.h, ib.l);
+}
+template <int S>
+__device__ __forceinline__ cdf subi(cdf a, cdf b) { return addi<-S>(a, b); }
 
 // Element type a compute type reads and writes at the operator's interface
 // (the FP64 vectors x, y for the double-word path), and the conversions.
@@ -200,7 +281,7 @@ template <typename T>
 __device__ __forceinline__ typename IOT<T>::E from_v(typename CT<T>::V v) { return v; }
 template <>
 __device__ __forceinline__ double2 from_v<df>(cdf v) {
-  return make_double2((double)v.x.hi + (double)v.x.lo, (double)v.y.hi + (double)v.y.lo);
+  return make_double2((double)v.h.x + (double)v.l.x, (double)v.h.y + (double)v.l.y);
 }
 
 // a * (S i) for S = +1 / -1
@@ -227,6 +308,21 @@ __device__ __forceinline__ V rot(V a, T c, T s) {
   r.y = fmadd(s, a.x, c * a.y);
   return r;
 }
+// c + s a for real s, and -a (overloaded for the packed double-word complex)
+template <typename T, typename V>
+__device__ __forceinline__ V cfma(T s, V a, V c) {
+  V r;
+  r.x = fmadd(s, a.x, c.x);
+  r.y = fmadd(s, a.y, c.y);
+  return r;
+}
+template <typename V>
+__device__ __forceinline__ V vneg(V a) {
+  V r;
+  r.x = -a.x;
+  r.y = -a.y;
+  return r;
+}
 
 // ------------------------------------------------------------ codelets
 // In-place DFT of length R on registers: U_q = sum_r u_r exp(S 2 pi i r q / R).
@@ -246,7 +342,7 @@ template <int S, typename T> struct Dft<3, S, T> {
   static __device__ __forceinline__ void run(V* u) {
     const T h3 = (T)0.86602540378443864676;  // sqrt(3)/2
     V t = u[1] + u[2];
-    V m = CT<T>::make(fmadd((T)-0.5, t.x, u[0].x), fmadd((T)-0.5, t.y, u[0].y));
+    V m = cfma((T)-0.5, t, u[0]);
     V d = h3 * (u[1] - u[2]);
     u[0] = u[0] + t;
     u[1] = addi<S>(m, d);
@@ -388,15 +484,8 @@ struct DftOdd {
         int j = (r * q) % R;
         const T cs = (T)OddRoots<R>::c(j <= H ? j : R - j);
         const T sn = (T)((j <= H) ? OddRoots<R>::s(j) : -OddRoots<R>::s(R - j));
-        A.x = fmadd(cs, a[r].x, A.x);
-        A.y = fmadd(cs, a[r].y, A.y);
-        if (r == 1) {
-          B.x = sn * b[r].x;
-          B.y = sn * b[r].y;
-        } else {
-          B.x = fmadd(sn, b[r].x, B.x);
-          B.y = fmadd(sn, b[r].y, B.y);
-        }
+        A = cfma(cs, a[r], A);
+        B = (r == 1) ? sn * b[r] : cfma(sn, b[r], B);
       }
       u[q] = addi<S>(A, B);
       u[R - q] = subi<S>(A, B);
