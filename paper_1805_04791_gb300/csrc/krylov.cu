@@ -95,9 +95,15 @@ vie_status run_rhs(vie_problem* P, const double* d, const double* p, int nrhs, v
 // one batched operator apply over the group and one batched reduction, with a
 // single device-to-host copy of all the group's Hessenberg columns.  Device
 // layout of a group: vectors [r][L] (r < nb); Krylov basis [i][r][L].
-static const int kRedBlocks = 608;  // 4 x 152 SMs
+static const int kRedBlocks = 608;  // 4 x 152 SMs: the most blocks a reduction uses
 static const int kRedThreads = 256;
 static const int kDotChunk = 8;
+// Blocks of a reduction over L elements: at least 8 elements per thread, so a
+// short vector does not pay for hundreds of idle blocks' reduction trees.
+static int red_blocks(long long L) {
+  const long long b = (L + 8LL * kRedThreads - 1) / (8LL * kRedThreads);
+  return (int)std::max<long long>(1, std::min<long long>(b, kRedBlocks));
+}
 
 // Per-thread accumulation type: FP64 for an FP64 basis; FP32 for an FP32
 // basis (each thread sums only ~L / 77824 terms in FP32 before the FP64
@@ -150,15 +156,18 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const TB* __restrict__
           ai[t] += v.x * we.y - v.y * we.x;
         }
     }
+    // warp sums in the accumulation type, for the slots in use only (cnt is
+    // block-uniform); the cross-warp and cross-block sums are FP64
 #pragma unroll
-    for (int t = 0; t < kDotChunk; ++t) {
-      double2 a = make_double2((double)ar[t], (double)ai[t]);
-      for (int off = 16; off > 0; off >>= 1) {
-        a.x += __shfl_down_sync(0xffffffffu, a.x, off);
-        a.y += __shfl_down_sync(0xffffffffu, a.y, off);
+    for (int t = 0; t < kDotChunk; ++t)
+      if (t < cnt) {
+        AT ax = ar[t], ay = ai[t];
+        for (int off = 16; off > 0; off >>= 1) {
+          ax += __shfl_down_sync(0xffffffffu, ax, off);
+          ay += __shfl_down_sync(0xffffffffu, ay, off);
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = make_double2((double)ax, (double)ay);
       }
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = a;
-    }
     __syncthreads();
     if (threadIdx.x < cnt) {
       double2 sm = make_double2(0, 0);
@@ -232,9 +241,8 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(TB* __restrict__ w, c
     wr[e] = acc;
     nn += acc.x * acc.x + acc.y * acc.y;
   }
-  double d = (double)nn;
-  for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  for (int off = 16; off > 0; off >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)nn;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0;
@@ -323,9 +331,10 @@ static int ldp_of(const Group& g) { return g.m + 3; }
 
 // norms of nb vectors [r][L] (FP64) -> host
 static vie_status norms_host(const double2* v, Group& g, std::vector<double>& out, cudaStream_t st) {
-  k_multidot<double2><<<dim3(kRedBlocks, g.nb), kRedThreads, 0, st>>>(v, 0, 0, v, g.L, g.partial, ldp_of(g), 1);
+  const int G = red_blocks(g.L);
+  k_multidot<double2><<<dim3(G, g.nb), kRedThreads, 0, st>>>(v, 0, 0, v, g.L, g.partial, ldp_of(g), 1);
   VIE_CK(cudaGetLastError());
-  k_reduce_partials<<<dim3(1, g.nb), 256, 0, st>>>(g.partial, 1, kRedBlocks, ldp_of(g), g.hdev, g.HS);
+  k_reduce_partials<<<dim3(1, g.nb), 256, 0, st>>>(g.partial, 1, G, ldp_of(g), g.hdev, g.HS);
   VIE_CK(cudaGetLastError());
   std::vector<double2> h((size_t)g.nb * g.HS);
   VIE_CK(cudaMemcpyAsync(h.data(), g.hdev, sizeof(double2) * g.nb * g.HS, cudaMemcpyDeviceToHost, st));
@@ -352,7 +361,8 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
   TB* V = (TB*)g.V;
   TB* w = (TB*)(sizeof(TB) == sizeof(double2) ? (void*)g.w64 : (void*)g.w32);
   const int prec = sizeof(TB) == sizeof(double2) ? VIE_FP64 : VIE_FP32;
-  const dim3 ewg(ew_blocks(L), nb), redg(kRedBlocks, nb);
+  const int G = red_blocks(L);
+  const dim3 ewg(ew_blocks(L), nb), redg(G, nb);
   std::vector<double> sc(nb);
   for (int r = 0; r < nb; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
   VIE_CK(cudaMemcpyAsync(g.sdev, sc.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
@@ -376,11 +386,11 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
     *applies += active;
     k_multidot<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j + 1, w, L, g.partial, ldp, 1);
     VIE_CK(cudaGetLastError());
-    k_reduce_partials<<<dim3(j + 2, nb), 256, 0, st>>>(g.partial, j + 2, kRedBlocks, ldp, g.hdev, HS);
+    k_reduce_partials<<<dim3(j + 2, nb), 256, 0, st>>>(g.partial, j + 2, G, ldp, g.hdev, HS);
     VIE_CK(cudaGetLastError());
     k_axpy_norm<TB><<<redg, kRedThreads, 0, st>>>(w, V, ldi, j + 1, g.hdev, HS, L, g.partial, ldp);
     VIE_CK(cudaGetLastError());
-    k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, kRedBlocks, ldp, g.hdev + (j + 2), HS);
+    k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, G, ldp, g.hdev + (j + 2), HS);
     VIE_CK(cudaGetLastError());
     VIE_CK(cudaMemcpyAsync(hb.data(), g.hdev, sizeof(double2) * nb * HS, cudaMemcpyDeviceToHost, st));
     VIE_CK(cudaStreamSynchronize(st));
@@ -390,11 +400,11 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
     if (reorth) {
       k_multidot<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j + 1, w, L, g.partial, ldp, 0);
       VIE_CK(cudaGetLastError());
-      k_reduce_partials<<<dim3(j + 1, nb), 256, 0, st>>>(g.partial, j + 1, kRedBlocks, ldp, g.hdev + H2, HS);
+      k_reduce_partials<<<dim3(j + 1, nb), 256, 0, st>>>(g.partial, j + 1, G, ldp, g.hdev + H2, HS);
       VIE_CK(cudaGetLastError());
       k_axpy_norm<TB><<<redg, kRedThreads, 0, st>>>(w, V, ldi, j + 1, g.hdev + H2, HS, L, g.partial, ldp);
       VIE_CK(cudaGetLastError());
-      k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, kRedBlocks, ldp, g.hdev + H2 + j + 1, HS);
+      k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, G, ldp, g.hdev + H2 + j + 1, HS);
       VIE_CK(cudaGetLastError());
       VIE_CK(cudaMemcpyAsync(hb.data(), g.hdev, sizeof(double2) * nb * HS, cudaMemcpyDeviceToHost, st));
       VIE_CK(cudaStreamSynchronize(st));
@@ -550,14 +560,15 @@ __global__ void __launch_bounds__(kRedThreads) k_dots4(Dots4 d, long long L, dou
         ai[t] += x.x * y.y - x.y * y.x;
       }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    double2 a = make_double2(ar[t], ai[t]);
-    for (int off = 16; off > 0; off >>= 1) {
-      a.x += __shfl_down_sync(0xffffffffu, a.x, off);
-      a.y += __shfl_down_sync(0xffffffffu, a.y, off);
+  for (int t = 0; t < 4; ++t)
+    if (t < d.k) {  // block-uniform
+      double2 a = make_double2(ar[t], ai[t]);
+      for (int off = 16; off > 0; off >>= 1) {
+        a.x += __shfl_down_sync(0xffffffffu, a.x, off);
+        a.y += __shfl_down_sync(0xffffffffu, a.y, off);
+      }
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = a;
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = a;
-  }
   __syncthreads();
   if (threadIdx.x < d.k) {
     double2 sm = make_double2(0, 0);
@@ -580,9 +591,10 @@ __global__ void k_lincomb(double2* y, const double2* x0, double2 a0, const doubl
 
 static vie_status dots_host(Dots4 d, long long L, double2* partial, double2* dev, std::vector<cd>& out,
                             cudaStream_t st) {
-  k_dots4<<<kRedBlocks, kRedThreads, 0, st>>>(d, L, partial);
+  const int G = red_blocks(L);
+  k_dots4<<<G, kRedThreads, 0, st>>>(d, L, partial);
   VIE_CK(cudaGetLastError());
-  k_reduce_partials<<<dim3(d.k, 1), 256, 0, st>>>(partial, d.k, kRedBlocks, 0, dev, 0);
+  k_reduce_partials<<<dim3(d.k, 1), 256, 0, st>>>(partial, d.k, G, 0, dev, 0);
   VIE_CK(cudaGetLastError());
   double2 h[4];
   VIE_CK(cudaMemcpyAsync(h, dev, sizeof(double2) * d.k, cudaMemcpyDeviceToHost, st));
