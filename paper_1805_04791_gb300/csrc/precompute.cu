@@ -7,6 +7,7 @@
 //    grid Nyquist cutoff (Sec. 5, step c), brought to the (2n)^3 convolution
 //    grid and stored as octants (the kernels are even or odd in each axis).
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -188,14 +189,15 @@ __global__ void k_build_F(double2* __restrict__ F, const double2* __restrict__ t
 }
 
 // Generic in-place FFT of a cubic M^3 FP64 array along one axis (0 x, 1 y, 2 z).
-template <int S>
-__global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan pl, const double2* __restrict__ twg,
-                           int nl) {
-  extern __shared__ double2 sm[];
+template <int S, typename T>
+__global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan pl,
+                           const typename CT<T>::V* __restrict__ twg, int nl) {
+  typedef typename CT<T>::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int LS = M + 1;
-  double2* tw = sm;
-  double2* b0 = tw + M;
-  double2* b1 = b0 + nl * LS;
+  V* tw = (V*)smraw;
+  V* b0 = tw + M;
+  V* b1 = b0 + nl * LS;
   const int tid = flat_tid(), nt = flat_nthreads();
   for (int j = tid; j < M; j += nt) tw[j] = twg[j];
   const long long MM = (long long)M * M;
@@ -208,14 +210,14 @@ __global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan 
   for (int idx = tid; idx < nl * M; idx += nt) {
     int l, j;
     if (axis == 0) { l = idx / M; j = idx - l * M; } else { j = idx / nl; l = idx - j * nl; }
-    b0[l * LS + j] = data[addr(l, j)];
+    b0[l * LS + j] = to_v<T>(data[addr(l, j)]);
   }
   __syncthreads();
-  double2* r = tile_fft<S, double>(b0, b1, pl, tw, nl, LS);
+  V* r = tile_fft<S, T>(b0, b1, pl, tw, nl, LS);
   for (int idx = tid; idx < nl * M; idx += nt) {
     int l, j;
     if (axis == 0) { l = idx / M; j = idx - l * M; } else { j = idx / nl; l = idx - j * nl; }
-    data[addr(l, j)] = r[l * LS + j];
+    data[addr(l, j)] = from_v<T>(r[l * LS + j]);
   }
 }
 
@@ -225,16 +227,17 @@ static int pick_nl(int M) {
   return nl;
 }
 
-template <int S>
-static vie_status fft_cube(double2* data, int M, const FftPlan& pl, const double2* tw, cudaStream_t st) {
+// In-place 3D DFT of an FP64 cube, lines along each axis in turn; arithmetic in
+// T (FP64, or double-word on the FP32 pipes), one block row per tile line.
+template <int S, typename T>
+static vie_status fft_cube(double2* data, int M, const FftPlan& pl, const typename CT<T>::V* tw, cudaStream_t st) {
   const int nl = pick_nl(M);
-  const size_t smem = sizeof(double2) * (M + 2 * nl * (M + 1));
-  VIE_CK(allow_smem(k_fft_cube<S>));
-  dim3 blk(std::max(1, std::min(32, M / 16)), 1);
-  blk.y = 256 / blk.x;
+  const size_t smem = sizeof(typename CT<T>::V) * (M + 2 * nl * (M + 1));
+  VIE_CK(allow_smem(k_fft_cube<S, T>));
+  const dim3 blk(std::max(1, std::min(32, M / 16)), nl);
   for (int axis = 0; axis < 3; ++axis) {
     dim3 grid = axis == 0 ? dim3((unsigned)((long long)M * M / nl), 1) : dim3(M / nl, M);
-    k_fft_cube<S><<<grid, blk, smem, st>>>(data, M, axis, pl, tw, nl);
+    k_fft_cube<S, T><<<grid, blk, smem, st>>>(data, M, axis, pl, tw, nl);
     VIE_CK(cudaGetLastError());
   }
   return VIE_OK;
@@ -310,6 +313,8 @@ static vie_status combine(vie_problem* P, KernelSet& K, int mode, const CombineD
 
 // Compute the raw octant kernels of the symbols in `mask` (bit = Sym) that are
 // not computed yet.
+static vie_status to_df(const double2* src, cdf** dst, long long count, cudaStream_t st);
+
 static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st) {
   mask &= ~P->sym_mask;
   if (!mask) return VIE_OK;
@@ -329,6 +334,16 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
   VIE_CK(dalloc((void**)&E, sizeof(double2) * M3, st));
   vie_status s = make_twiddles(sn, &tw_sn, &tw_sn32, st);
   if (s != VIE_OK) return s;
+  // the kernel-transform FFTs run in double-word arithmetic (FP64 accuracy on
+  // the FP32 pipes); VIE_SETUP_FP64=1 keeps them in native FP64
+  const char* e64 = getenv("VIE_SETUP_FP64");
+  const bool dw = !(e64 && e64[0] == '1');
+  cdf *tw_sndf = nullptr, *tw_2ndf = nullptr;
+  if (dw) {
+    s = to_df(tw_sn, &tw_sndf, sn, st);
+    if (s == VIE_OK) s = to_df(P->tw64, &tw_2ndf, M, st);
+    if (s != VIE_OK) return s;
+  }
   FftPlan plsn;
   if (!make_plan(sn, &plsn)) {
     set_error("bad oversampled grid size");
@@ -339,11 +354,11 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
     if (!(mask & (1u << sym))) continue;
     k_build_F<<<gb, 256, 0, st>>>(F, tab, sn, sym, dk);
     VIE_CK(cudaGetLastError());
-    s = fft_cube<+1>(F, sn, plsn, tw_sn, st);
+    s = dw ? fft_cube<+1, df>(F, sn, plsn, tw_sndf, st) : fft_cube<+1, double>(F, sn, plsn, tw_sn, st);
     if (s != VIE_OK) return s;
     k_embed<<<gb, 256, 0, st>>>(F, E, n, sn, 1.0 / (double)S3);
     VIE_CK(cudaGetLastError());
-    s = fft_cube<-1>(E, M, P->plan2n, P->tw64, st);
+    s = dw ? fft_cube<-1, df>(E, M, P->plan2n, tw_2ndf, st) : fft_cube<-1, double>(E, M, P->plan2n, P->tw64, st);
     if (s != VIE_OK) return s;
     k_octant<<<gb, 256, 0, st>>>(E, P->sym_oct + (long long)sym * O3, n);
     VIE_CK(cudaGetLastError());
@@ -353,6 +368,8 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
   dfree(tab, st);
   dfree(tw_sn, st);
   dfree(tw_sn32, st);
+  dfree(tw_sndf, st);
+  dfree(tw_2ndf, st);
   P->sym_mask |= mask;
   return VIE_OK;
 }
