@@ -68,7 +68,8 @@ def parse():
                     help="comma list of extra legs: batched (Maxwell 128^3 with mu, 64 plane waves, lockstep "
                          "GMRES), maxwell256 (Maxwell 256^3 with mu: mixed vs FP64 time to 1e-8), serve "
                          "(continuous-batching request mix), paper (Bi-CGStab matvec counts on the paper's "
-                         "media beside Tables 2-5), laplace32 (electrostatic 32^3 FP64 solve to 1e-10)")
+                         "media beside Tables 2-5), laplace32 (electrostatic 32^3 FP64 solve to 1e-10), "
+                         "serve_sweep (the request mix at arrival rates 10..500 /s; not in the default run)")
     ap.add_argument("--paper-n", type=int, default=70)
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -327,6 +328,26 @@ def leg_serve(args, dev):
     return out
 
 
+def leg_serve_sweep(args, dev):
+    """The serving mix at arrival rates 10, 20, 50, 100, 200, 500 /s (--serve-requests
+    requests each, fresh server per rate, after one unreported warm-up mix):
+    p50/p99 latency and solves/s per rate."""
+    from paper_1805_04791_gb300 import serve
+    import vie_inputs as vi
+
+    # warm-up (not reported): the first request of each shape tunes its z pass
+    serve.Server(budget_bytes=160e9, max_slots=32, restart=30, tol=1e-8).run(
+        vi.serving_mix(args.serve_requests, rate_per_s=500.0, seed=2))
+    out = {}
+    for rate in (10.0, 20.0, 50.0, 100.0, 200.0, 500.0):
+        reqs = vi.serving_mix(args.serve_requests, rate_per_s=rate, seed=1)
+        srv = serve.Server(budget_bytes=160e9, max_slots=32, restart=30, tol=1e-8)
+        st = srv.run(reqs).summary()
+        out[str(int(rate))] = {k: st[k] for k in ("completed", "failed", "p50_latency_s", "p99_latency_s",
+                                                  "solves_per_s", "peak_inflight") if k in st}
+    return out
+
+
 def leg_paper(args, dev):
     """Bi-CGStab (the paper's solver) on the paper's four media (Sec. 5.2, [0,1]^3,
     E_in = (0, 0, exp(i w x))) at n = --paper-n, FP64, tolerance 1e-12; matvec counts
@@ -565,7 +586,7 @@ def run_ours(args):
     for leg in [x for x in args.legs.split(",") if x]:
         t0 = time.perf_counter()
         fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve, "paper": leg_paper,
-              "laplace32": leg_laplace32}[leg]
+              "laplace32": leg_laplace32, "serve_sweep": leg_serve_sweep}[leg]
         try:
             extra[leg] = fn(args, dev)
         except Exception as e:  # report, do not lose the main line
