@@ -522,26 +522,47 @@ def run_ours(args):
     del xs64, ys64
 
     # ---------------- end to end through the C ABI with host buffers
+    # Every step uploads its input from pinned host memory, applies the operator
+    # and downloads the result.  Steps are pipelined the way a streaming caller
+    # would run them: upload of step i+1 and download of step i-1 on their own
+    # streams overlap the apply of step i (two device buffer pairs, event-ordered).
     xh = [torch.empty((c, n, n, n), dtype=torch.complex64, pin_memory=True) for _ in range(2)]
-    yh = [torch.empty_like(xh[0]) for _ in range(2)]
+    yh = [torch.empty((c, n, n, n), dtype=torch.complex64, pin_memory=True) for _ in range(2)]  # pinned too
     for i in range(2):
         xh[i].copy_(xs[i].cpu())
-    xd, yd = xs[0], ys[0]
+    xd, yd = xs[:2], ys[:2]
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_ap = [torch.cuda.Event() for _ in range(2)]
+    ev_dn = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_ap + ev_dn:
+        e.record(stream)
+
+    def e2e_steps(count):
+        for i in range(count):
+            b = i % 2
+            with torch.cuda.stream(s_up):
+                s_up.wait_event(ev_ap[b])  # the apply that last read xd[b] is done
+                xd[b].copy_(xh[b], non_blocking=True)
+                ev_up[b].record(s_up)
+            stream.wait_event(ev_up[b])
+            stream.wait_event(ev_dn[b])  # the download that last read yd[b] is done
+            P.apply(xd[b], yd[b], vie.VIE_FP32, 1, stream)
+            ev_ap[b].record(stream)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(ev_ap[b])
+                yh[b].copy_(yd[b], non_blocking=True)
+                ev_dn[b].record(s_down)
+
     ke = max(5, min(50, args.steps // 4))
-    for i in range(2):
-        xd.copy_(xh[i], non_blocking=True)
-        P.apply(xd, yd, vie.VIE_FP32)
-        yh[i].copy_(yd, non_blocking=True)
+    e2e_steps(4)
     torch.cuda.synchronize()
     te = time.perf_counter()
-    for i in range(ke):
-        xd.copy_(xh[i % 2], non_blocking=True)
-        P.apply(xd, yd, vie.VIE_FP32)
-        yh[i % 2].copy_(yd, non_blocking=True)
+    e2e_steps(ke)
     torch.cuda.synchronize()
     te = time.perf_counter() - te
     e2e = {"value": world * ke / te, "unit": "applies/s", "h2d_bytes_per_step": xh[0].numel() * 8,
-           "d2h_bytes_per_step": yh[0].numel() * 8}
+           "d2h_bytes_per_step": yh[0].numel() * 8, "pipelined": "upload i+1 | apply i | download i-1"}
     del xh, yh
 
     # ---------------- time to 1e-8 residual, mixed vs FP64
