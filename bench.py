@@ -87,6 +87,20 @@ def dist_env():
     return rank, world, local
 
 
+def replica_timing(total_ms, steps, world, device=None):
+    """Job time = the slowest rank's time (all-reduce MAX over the process
+    group); whole-job rate = world x steps / job time (every rank runs one
+    replica of the same workload)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -488,13 +502,7 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    applies_per_s = world * args.steps / (total_ms / 1000.0)
+    total_ms, applies_per_s = replica_timing(total_ms, args.steps, world, dev)
 
     # ---------------- per-kernel timing of the same workload (event-bracketed passes)
     kreps = min(args.steps, 100)
