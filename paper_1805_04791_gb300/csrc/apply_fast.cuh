@@ -308,15 +308,23 @@ f_p3b(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
 // mixing reads only shared memory.  The line pitch of the transpose buffers
 // is chosen so that 8 pencils x 2 threads (FP32) or 8 pencils (FP64) hit
 // distinct banks.
-template <int MODE, int NP, int R2>
+template <typename T, int R1, int R2, int MODE, int NP>
 struct P3cThreads {
   static constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
+  static constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
   static constexpr int N = NP * R2 * CMAX;
-  static constexpr int MINB = N <= 384 ? 2 : 1;
+  static constexpr int M = R1 * R2;
+  static constexpr int ESZ = (int)sizeof(typename CT<T>::V);
+  static constexpr int LS0 = Fft2<T, R1, R2>::LS0;
+  static constexpr int LS = (ESZ == 8) ? ((LS0 + 13) / 16) * 16 + 2 : (LS0 | 1);
+  // shared memory of a CTA (2n fixes n, hence the slab extent): two CTAs per
+  // SM (and registers capped for them) only where two fit
+  static constexpr long long SMEM = (long long)ESZ * (M + (long long)CMAX * NP * LS + (long long)NARR * (M / 2 + 1) * (NP + 1));
+  static constexpr int MINB = (N <= 384 && SMEM <= 112 * 1024) ? 2 : 1;
 };
 
 template <typename T, int R1, int R2, int MODE, int NP>
-__global__ void __launch_bounds__(P3cThreads<MODE, NP, R2>::N, P3cThreads<MODE, NP, R2>::MINB)
+__global__ void __launch_bounds__(P3cThreads<T, R1, R2, MODE, NP>::N, P3cThreads<T, R1, R2, MODE, NP>::MINB)
 f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* __restrict__ K,
       const typename CT<T>::V* __restrict__ twg) {
   typedef Fft2<T, R1, R2> F;
@@ -873,9 +881,9 @@ struct FastPath {
     constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
     constexpr int LS = (sizeof(V) == 8) ? ((F::LS0 + 13) / 16) * 16 + 2 : (F::LS0 | 1);
     constexpr int NTX = M / NP;
-    constexpr int NTHR = P3cThreads<MODE, NP, R2>::N;
+    constexpr int NTHR = P3cThreads<T, R1, R2, MODE, NP>::N;
     const size_t sm = sizeof(V) * (M + (size_t)CMAX * NP * LS + (size_t)NARR * (n + 1) * (NP + 1));
-    const size_t cap = P3cThreads<MODE, NP, R2>::MINB == 2 ? 112 * 1024 : 224 * 1024;
+    const size_t cap = 224 * 1024;
     *done = false;
     if constexpr (NTHR > 1024 || NTX < 2) {
       return VIE_OK;  // shape not expressible: not instantiated

@@ -373,6 +373,45 @@ def test_every_zpass_variant_matches_oracle(vie, monkeypatch, variant, kind, n, 
         pytest.skip(f"variant {variant} does not apply to {kind} n={n}")
 
 
+def test_zpass_variants_at_2n_512(vie, monkeypatch):
+    """Maxwell with mu at 256^3 (2n = 512, the largest z-pass shapes): every
+    variant that fits reproduces the FP64 apply of the same input in FP32; the
+    FP64 path at this size is the one the smaller full-size tests pin to the
+    oracle.  At least one mirror-group variant must apply here."""
+    import torch
+
+    n = 256
+    p = vi.maxwell_problem(n=n, wavelengths=10.0, with_mu=True, seed=0)
+    eps, mu = eps_dev(p), mu_dev(p)
+    g = torch.Generator(device="cuda:0")
+    g.manual_seed(3)
+    x = torch.randn((6, n, n, n), dtype=torch.complex64, device="cuda:0", generator=g)
+    y64 = torch.empty((6, n, n, n), dtype=torch.complex128, device="cuda:0")
+    P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, eps, mu)
+    P.apply(x.to(torch.complex128), y64, vie.VIE_FP64)
+    P.close()
+    ran = []
+    for v in range(vie.P3_VARIANTS):
+        monkeypatch.setenv("VIE_P3_VARIANT", str(v))
+        P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, eps, mu)
+        try:
+            y32 = torch.empty_like(x)
+            try:
+                P.apply(x, y32, vie.VIE_FP32)
+            except vie.VieError as e:
+                assert e.status == vie.VIE_EINVAL
+                continue
+            torch.cuda.synchronize()
+            assert P.tune(vie.VIE_FP32) == v
+            err = float(torch.linalg.vector_norm(y32.to(torch.complex128) - y64) / torch.linalg.vector_norm(y64))
+            assert err <= 2e-5, (v, err)
+            ran.append(v)
+        finally:
+            P.close()
+            monkeypatch.delenv("VIE_P3_VARIANT", raising=False)
+    assert any(v in ran for v in (0, 1, 2)), ran
+
+
 def test_tune_entry_point(vie):
     p, P, op = setup(vie, "helmholtz", 24, 4.0, False)
     import paper_1805_04791_gb300 as m
