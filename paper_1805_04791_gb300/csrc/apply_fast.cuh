@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <vector>
 
 #include "vie_fft2.cuh"
 #include "vie_internal.h"
@@ -1047,11 +1048,12 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
 // 8, 16 or 4 pencils, one tile per CTA with 8 pencils, lane-pair
 // mirror-group CTAs with 8, 16 or 4 pencils, component-group mirror-group
 // CTAs with 8, 4 or 16 pencils, or component-group CTAs of 8 or 4 pencils
-// sized to the device, each walking several mirror groups) is launched once
-// to warm up and then timed over 3 launches with CUDA events on the buffer B
-// (whose contents are scratch at this point); the fastest is kept for the
-// problem's (precision, mode).  VIE_TUNE=0 takes the first applicable variant;
-// VIE_P3_VARIANT=k forces variant k.
+// sized to the device, each walking several mirror groups) runs once untimed
+// (a pass over all candidates, which also brings the clocks up), then two
+// rounds of 3 launches timed with CUDA events on the buffer B (whose contents
+// are scratch at this point); each keeps its best round and the fastest is
+// kept for the problem's (precision, mode).  VIE_TUNE=0 takes the first
+// applicable variant; VIE_P3_VARIANT=k forces variant k.
 static const int kP3Variants = 12;
 static const int kP3Generic = 99;
 
@@ -1064,40 +1066,50 @@ vie_status tune_p3(vie_problem* P, const KernelSet& K, typename CT<T>::V* B, int
   const char* tune = getenv("VIE_TUNE");
   const bool timed = !(tune && tune[0] == '0');
   *best = -1;
-  bool timed_forced = false;
-  float best_ms = 1e30f;
-  cudaEvent_t e0, e1;
-  VIE_CK(cudaEventCreate(&e0));
-  VIE_CK(cudaEventCreate(&e1));
+  // applicable variants, each launched once untimed (this also brings the
+  // clocks up, so that the first candidates are not timed while they ramp)
+  std::vector<int> cand;
   for (int v = 0; v < kP3Variants; ++v) {
     if (force && atoi(force) != v) continue;
-    if (force) timed_forced = true;
     bool done = false;
     vie_status s = FP::p3v(v, B, P->n, C, Prec<T>::K(K), K.mode, 1, tw, &done, st);
     if (s != VIE_OK) return s;
-    if (!done) continue;
-    if (!timed || force) {
-      *best = v;
-      break;
-    }
-    VIE_CK(cudaEventRecord(e0, st));
-    for (int r = 0; r < 3; ++r) FP::p3v(v, B, P->n, C, Prec<T>::K(K), K.mode, 1, tw, &done, st);
-    VIE_CK(cudaEventRecord(e1, st));
-    VIE_CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    VIE_CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      *best = v;
-    }
+    if (done) cand.push_back(v);
   }
+  if (cand.empty()) {
+    if (force) {
+      set_error("forced z-pass variant does not apply to this shape");
+      return VIE_EINVAL;
+    }
+    *best = kP3Generic;  // no register-resident variant fits: generic kernel
+    return VIE_OK;
+  }
+  if (!timed || force || cand.size() == 1) {
+    *best = cand[0];
+    return VIE_OK;
+  }
+  // two rounds of 3 timed launches per candidate; each keeps its best round
+  std::vector<float> ms(cand.size(), 1e30f);
+  cudaEvent_t e0, e1;
+  VIE_CK(cudaEventCreate(&e0));
+  VIE_CK(cudaEventCreate(&e1));
+  for (int round = 0; round < 2; ++round)
+    for (size_t c = 0; c < cand.size(); ++c) {
+      bool done = false;
+      VIE_CK(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) FP::p3v(cand[c], B, P->n, C, Prec<T>::K(K), K.mode, 1, tw, &done, st);
+      VIE_CK(cudaEventRecord(e1, st));
+      VIE_CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      VIE_CK(cudaEventElapsedTime(&t, e0, e1));
+      ms[c] = std::min(ms[c], t);
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (*best < 0 && timed_forced) {
-    set_error("forced z-pass variant does not apply to this shape");
-    return VIE_EINVAL;
-  }
-  if (*best < 0) *best = kP3Generic;  // no register-resident variant fits: generic kernel
+  size_t b = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (ms[c] < ms[b]) b = c;
+  *best = cand[b];
   return VIE_OK;
 }
 
