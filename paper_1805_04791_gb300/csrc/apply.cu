@@ -417,7 +417,8 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     if (rec) VIE_CK(cudaEventRecord(ev[3], st));
   } else {
     int nl = pow2_divisor(M, 8);
-    while (nl > 1 && vs * (M + 2 * C * nl * (M + 1)) > 200 * 1024) nl >>= 1;
+    // two CTAs per SM: the z pass is compute bound and needs the warps
+    while (nl > 1 && vs * (M + 2 * C * nl * (M + 1)) > 110 * 1024) nl >>= 1;
     const size_t smem = vs * (M + 2 * C * nl * (M + 1));
     VIE_CK(allow_smem(k_p3<T>));
     dim3 grid(M / nl, M, nrhs);
