@@ -795,16 +795,20 @@ __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict_
   V* s = sm + l * F::LS;
   V uo[CO][H2];
   __syncthreads();
-#pragma unroll
-  for (int c = 0; c < CO; ++c) {
-    if (c >= cout) break;
+  // component c + 1's row is loaded while component c is transformed
+  V X[F::J][R2], Xn[F::J][R2];
+  auto load_row = [&](int c, V (*D)[R2]) {
     const V* src = A + ((long long)b * C + c) * cs + (long long)row * M;
-    V X[F::J][R2];
 #pragma unroll
     for (int j = 0; j < F::J; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2)
-        X[j][k2] = (ok && F::row(t, j)) ? src[t + R2 * j + R1 * k2] : CT<T>::make(0, 0);
+      for (int k2 = 0; k2 < R2; ++k2) D[j][k2] = (ok && F::row(t, j)) ? src[t + R2 * j + R1 * k2] : CT<T>::make(0, 0);
+  };
+  load_row(0, X);
+#pragma unroll
+  for (int c = 0; c < CO; ++c) {
+    if (c >= cout) break;
+    if (c + 1 < CO && c + 1 < cout) load_row(c + 1, Xn);
     F::invA(X, t, s, tw);
     __syncthreads();
     V u[R1];
@@ -812,6 +816,10 @@ __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict_
 #pragma unroll
     for (int n1 = 0; n1 < H2; ++n1) uo[c][n1] = u[n1];
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < F::J; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) X[j][k2] = Xn[j][k2];
   }
   if (!ok) return;
 #pragma unroll
