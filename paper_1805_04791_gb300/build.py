@@ -21,7 +21,7 @@ LIB = os.path.join(LIBDIR, "libvie_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-SOURCES = ["capi.cu", "precompute.cu", "apply.cu", "krylov.cu", "apply_static.cu"] + [
+SOURCES = ["capi.cu", "precompute.cu", "apply.cu", "krylov.cu", "apply_static.cu", "apply_fast_dw_256.cu"] + [
     f"apply_fast_{m:03d}.cu" for m in (64, 96, 128, 192, 256, 384, 512)]
 
 

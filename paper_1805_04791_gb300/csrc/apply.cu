@@ -301,7 +301,16 @@ static std::map<long long, int>& tune_cache() {
 
 
 static vie_status fast_dispatch(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                                bool with_identity, void* A, void* B, int C, int prec, cudaStream_t st) {
+                                bool with_identity, void* A, void* B, int C, int prec, cudaStream_t st,
+                                bool* used = nullptr) {
+  if (prec == VIE_DF64) {
+    bool u = true;
+    vie_status e = (2 * P->n == 256) ? fast_pass_dw_256(pass, P, K, in, out, nrhs, with_identity, A, B, C, st, &u)
+                                     : VIE_EINVAL;
+    if (used) *used = u;
+    if (e == VIE_EINVAL) set_error("no double-word fast path for this size");
+    return e;
+  }
   switch (2 * P->n) {
 #define VIE_CASE(MM, RA, RB) \
   case MM: return fast_pass_##MM(prec == VIE_FP64, pass, P, K, in, out, nrhs, with_identity, A, B, C, st);
@@ -358,9 +367,16 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
 
   // double-word arithmetic runs on the generic kernels only: its fully
   // unrolled register-resident variants take far too long to compile
-  FastSel fs = (Prec<T>::id == VIE_DF64) ? FastSel() : fast_select(M, K.mode, with_identity);
+  FastSel fs = fast_select(M, K.mode, with_identity);
+  if (Prec<T>::id == VIE_DF64) {
+    // double-word fast kernels exist for 2n = 256 and the operator's kernel sets
+    // only; its register-resident P5 (254 registers, one CTA per SM) is slower
+    // than the generic one, which it keeps
+    if (!(M == 256 && fs.p1 && (K.mode == KM_SYM3 || K.mode == KM_MAXWELL6))) fs = FastSel();
+    fs.p5 = false;
+  }
   int& p3v = P->p3_variant[Prec<T>::id][K.mode];
-  if (fs.p3 && p3v < 0) {
+  if (fs.p3 && p3v < 0 && Prec<T>::id != VIE_DF64) {  // the double-word z pass has one fixed schedule
     // one decision per (n, precision, mode) per process: every problem of a
     // shape then runs the same arithmetic (bitwise-reproducible results).  A
     // variant forced with VIE_P3_VARIANT bypasses the cache both ways.
@@ -412,10 +428,13 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   }
   // P3
   if (fs.p3) {
-    vie_status e = fast_dispatch(3, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
+    bool used = true;
+    vie_status e = fast_dispatch(3, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st, &used);
     if (e != VIE_OK) return e;
-    if (rec) VIE_CK(cudaEventRecord(ev[3], st));
-  } else {
+    if (!used) fs.p3 = false;  // no fast z pass fits this shape: the generic one below
+    else if (rec) VIE_CK(cudaEventRecord(ev[3], st));
+  }
+  if (!fs.p3) {
     int nl = pow2_divisor(M, 8);
     // two CTAs per SM: the z pass is compute bound and needs the warps
     while (nl > 1 && vs * (M + 2 * C * nl * (M + 1)) > 110 * 1024) nl >>= 1;

@@ -284,7 +284,7 @@ f_p3b(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
         for (int i = 0; i < NT; ++i) {
           if (i >= ntm) break;
           V kv = kp[i][zoff];
-          if (neg0[i] != (zodd[i] && fz)) { kv.x = -kv.x; kv.y = -kv.y; }
+          if (neg0[i] != (zodd[i] && fz)) kv = vneg(kv);
           acc = acc + cmul(kv, xs[i][k]);
         }
         X[j][k2] = acc;
@@ -408,19 +408,15 @@ f_p3c(typename CT<T>::V* __restrict__ B, int n, int C, const typename CT<T>::V* 
           // k < n for k2 < R2/2 and k > n for k2 > R2/2 (k = R1 k2 + [0, R1)); only k2 = R2/2 depends on t, j
           const bool fz = (k2 < R2 / 2) ? false : ((k2 > R2 / 2) ? true : (k > n));
           const int zoff = (fz ? M - k : k) * QW;
-          T ax = 0, ay = 0;
+          V acc = CT<T>::make(0, 0);
 #pragma unroll
           for (int i = 0; i < NT; ++i) {
             if (i >= ntm) break;
             const V kv = kp[i][zoff];
             const V xv = xs[i][k];
-            const T sgn = fz ? sg1[i] : sg0[i];
-            const T px = kv.x * xv.x - kv.y * xv.y;
-            const T py = kv.x * xv.y + kv.y * xv.x;
-            ax = fmadd(sgn, px, ax);
-            ay = fmadd(sgn, py, ay);
+            acc = cfma(fz ? sg1[i] : sg0[i], cmul(kv, xv), acc);
           }
-          X[j][k2] = CT<T>::make(ax, ay);
+          X[j][k2] = acc;
         }
     }
     __syncthreads();
@@ -1120,6 +1116,45 @@ vie_status tune_p3(vie_problem* P, const KernelSet& K, typename CT<T>::V* B, int
   *best = cand[b];
   return VIE_OK;
 }
+
+// Double-word (VIE_DF64) fast path: the register-resident P1, P2, P4 and the
+// mirror-group z pass for the operator's kernel sets only (3x3 symmetric,
+// Maxwell 6x6), one fixed schedule each (8 pencils per tile, 4 for Maxwell),
+// no tuning.  Instantiated for 2n = 256 only, in its own translation unit
+// (apply_fast_dw_256.cu): the unrolled double-word codelets are long to
+// compile, so every other shape and mode keeps the generic kernels.
+// *used = false if this (pass, mode) has no double-word fast kernel.
+template <int R1, int R2>
+vie_status fast_pass_dw(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
+                        bool with_identity, cdf* A, cdf* B, int C, cudaStream_t st, bool* used) {
+  typedef FastPath<df, R1, R2> FP;
+  const int n = P->n;
+  const cdf* tw = Prec<df>::tw(P);
+  const int cin = cin_of(K.mode), cout = cout_of(K.mode);
+  *used = true;
+  switch (pass) {
+    case 1: return FP::p1((const double2*)in, A, n, C, cin, nrhs, tw, st);
+    case 2: return FP::template py<-1>(A, B, n, C, cin, nrhs, tw, st);
+    case 3: {
+      bool done = false;
+      vie_status e = VIE_OK;
+      if (K.mode == KM_SYM3) {
+        e = FP::template p3c<KM_SYM3, 8>(B, n, C, Prec<df>::K(K), nrhs, tw, &done, st);
+        if (e == VIE_OK && !done) e = FP::template p3c<KM_SYM3, 4>(B, n, C, Prec<df>::K(K), nrhs, tw, &done, st);
+      } else if (K.mode == KM_MAXWELL6) {
+        e = FP::template p3c<KM_MAXWELL6, 4>(B, n, C, Prec<df>::K(K), nrhs, tw, &done, st);
+      }
+      if (e == VIE_OK && !done) *used = false;
+      return e;
+    }
+    case 4: return FP::template py<+1>(B, A, n, C, cout, nrhs, tw, st);
+    default:
+      return FP::p5(A, (const double2*)in, (double2*)out, n, C, cout, Prec<df>::He(P),
+                    P->has_mu ? Prec<df>::Hm(P) : nullptr, with_identity, nrhs, tw, st);
+  }
+}
+vie_status fast_pass_dw_256(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
+                            bool wid, void* A, void* B, int C, cudaStream_t st, bool* used);
 
 // Per-size entry points (one translation unit each).
 #define VIE_FAST_SIZES(X) X(64, 8, 8) X(96, 12, 8) X(128, 16, 8) X(192, 24, 8) X(256, 16, 16) X(384, 24, 16) X(512, 32, 16)

@@ -72,7 +72,7 @@ def test_apply_df64_full_size_and_batched(vie):
         torch.cuda.synchronize()
         assert rel(ydf[0].cpu().numpy(), y64.cpu().numpy()) <= 1e-12
         assert torch.equal(ydf[1], y1)
-        assert P.tune(vie.VIE_DF64) == -1  # generic kernels: no z-pass schedule to pick
+        assert P.tune(vie.VIE_DF64) == -1  # one fixed double-word schedule: nothing to tune
     finally:
         P.close()
 
@@ -111,5 +111,26 @@ def test_mixed_solve_with_double_word_residuals(vie, monkeypatch, case):
         torch.cuda.synchronize()
         true_res = float(torch.linalg.vector_norm(r - b) / torch.linalg.vector_norm(b))
         assert true_res <= 1.5e-10
+    finally:
+        P.close()
+
+
+def test_apply_df64_maxwell_128_fast_path(vie):
+    """Maxwell with mu at 128^3 (2n = 256: the register-resident double-word
+    passes and 6x6 z pass) equals the FP64 apply to FP64-level accuracy."""
+    import torch
+
+    p = vi.maxwell_problem(n=128, wavelengths=5.0, with_mu=True, seed=1)
+    P = vie.Problem("maxwell", 128, p.lo, p.hi, p.omega, eps_dev(p), mu_dev(p))
+    try:
+        g = torch.Generator(device="cuda:0")
+        g.manual_seed(6)
+        x = torch.randn((6, 128, 128, 128), dtype=torch.complex128, device="cuda:0", generator=g)
+        y64 = torch.empty_like(x)
+        ydf = torch.empty_like(x)
+        P.apply(x, y64, vie.VIE_FP64)
+        P.apply(x, ydf, vie.VIE_DF64)
+        torch.cuda.synchronize()
+        assert rel(ydf.cpu().numpy(), y64.cpu().numpy()) <= 1e-12
     finally:
         P.close()
