@@ -6,8 +6,8 @@ Tolerances (relative L2 over all components):
 * FP32 apply: 2e-5.  Each FFT stage adds ~eps_32 = 6e-8 relative error; a
   pruned forward plus inverse 3D transform on (2n)^3 has 2 log2((2n)^3) ~ 50
   butterfly levels at 2n = 256, i.e. ~3e-6 -- the tolerance leaves a 6x margin.
-* FP64 solve: 1e-10 (spec bound for FP64 paths); mixed solve: 1e-6 after
-  refinement (spec bound), tested here at a tighter 1e-8.
+* FP64 solve: 1e-10 (the parity bound for FP64 paths); mixed solve: the bound
+  after refinement is 1e-6, tested here at a tighter 1e-8.
 """
 import math
 
