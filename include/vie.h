@@ -148,7 +148,8 @@ vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int 
  *   scratch it did not write first); calls that overlap on the GPU -- on
  *   different streams or different handles -- race on it and must be ordered
  *   by the caller.
- *   x, y, precision, nrhs, stream: as for vie_apply. */
+ *   x, y, nrhs, stream: as for vie_apply; precision VIE_FP64 or VIE_FP32
+ *   (VIE_DF64 returns VIE_EINVAL). */
 vie_status vie_apply_static(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
 
 /* Right-hand sides for plane-wave (or uniform-field) incidence, FP64 complex,
@@ -199,7 +200,9 @@ vie_status vie_problem_destroy(vie_problem* P);
  * CTAs of 8/4/16 pencils with all three components of a vector per thread;
  * 10/11 as 7/8 with a grid sized to the device, each CTA walking several
  * mirror groups and prefetching the next one's inputs and kernel values.
- * vie_apply
+ * Every candidate runs once untimed, then two rounds of three timed launches;
+ * each keeps its best round and the fastest is chosen.  VIE_DF64 has one fixed
+ * schedule (*variant = -1).  vie_apply
  * tunes on its first call for a precision anyway; calling vie_tune first keeps
  * the tuning time out of a timed or captured region.  Synchronises the stream.
  * Environment: VIE_TUNE=0 takes the first applicable variant without timing,
