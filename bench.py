@@ -71,7 +71,9 @@ def parse():
                          "GMRES), maxwell256 (Maxwell 256^3 with mu: mixed vs FP64 time to 1e-8), serve "
                          "(continuous-batching request mix), paper (Bi-CGStab matvec counts on the paper's "
                          "media beside Tables 2-5), laplace32 (electrostatic 32^3 FP64 solve to 1e-10), "
-                         "serve_sweep (the request mix at arrival rates 10..500 /s; not in the default run)")
+                         "serve_sweep (the request mix at arrival rates 10..500 /s), selfconv (E_2 / E_inf "
+                         "self-convergence on the paper's media, 30/42/70 against 210; the last two are not in "
+                         "the default run)")
     ap.add_argument("--paper-n", type=int, default=70)
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -401,6 +403,61 @@ def leg_paper(args, dev):
     return out
 
 
+def leg_selfconv(args, dev):
+    """Self-convergence on the paper's media (Sec. 5.2; the E_2 / E_inf columns of
+    Tables 2-5): reduced Maxwell, E_in = (0, 0, exp(i w x)) on [0,1]^3, FP64 GMRES to
+    1e-12 on 30-, 42- and 70-grids and on a 210-grid that nests all three (odd ratios
+    7, 5, 3); eps444, which the paper tabulates at n = 50, 100, ..., on 30- and
+    50-grids against a 150-grid.  Errors are relative, over all components of J, on
+    the coarse nodes.  The paper's printed errors at its smallest grid (its reference
+    solution is not stated) are reported beside ours."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as f:
+        table = json.load(f)["rows"]
+    grids = {"eps444": (150, (30, 50))}
+    d, pol = np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0])
+
+    def solve(medium, size, n):
+        eps = torch.from_numpy(vi.paper_medium(medium, n, 0.0, 1.0).reshape(9, -1).copy()).to(dev)
+        P = vie.Problem("maxwell", n, 0.0, 1.0, 2 * np.pi * size, eps)
+        b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
+        P.rhs(d, pol, 1, b)
+        J = torch.zeros_like(b)
+        t0 = time.perf_counter()
+        st, info = P.solve(b, J, tol=1e-12, restart=60, max_outer=40, mode=vie.VIE_SOLVE_FP64)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        P.close()
+        return J, info, dt
+
+    out = {"equation": "maxwell_reduced", "tol": 1e-12, "rows": []}
+    for medium in ("eps222", "eps234", "eps_dense", "eps444"):
+        nref, coarse = grids.get(medium, (210, (30, 42, 70)))
+        for size in (1e-10, 1.0):
+            Jr, info_r, t_r = solve(medium, size, nref)
+            row = {"medium": medium, "size": size, "n_ref": nref, "ref_gmres_iters": info_r.inner_iters,
+                   "ref_solve_s": t_r,
+                   "paper": [{"n": r["n"], "E2": r["E2"], "Einf": r["Einf"]} for r in table
+                             if r["medium"] == medium and r["n"] == coarse[-1] and r["size_wavelengths"] == size],
+                   "errors": {}}
+            for n in coarse:
+                s = vi.nested_nodes(n, nref)
+                ref = Jr[:, s, s, s]
+                J, _, _ = solve(medium, size, n)
+                row["errors"][str(n)] = {
+                    "E2": float(torch.linalg.vector_norm(J - ref) / torch.linalg.vector_norm(ref)),
+                    "Einf": float((J - ref).abs().max() / ref.abs().max())}
+                del J, ref
+            out["rows"].append(row)
+            del Jr
+            torch.cuda.empty_cache()
+    return out
+
+
 def leg_laplace32(args, dev):
     """Electrostatic workload: anisotropic Laplace bump, 32^3 on [-1,1]^3, uniform E0 = z,
     FP64 GMRES to 1e-10 (time to solution over repeated solves)."""
@@ -619,7 +676,7 @@ def run_ours(args):
     for leg in [x for x in args.legs.split(",") if x]:
         t0 = time.perf_counter()
         fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve, "paper": leg_paper,
-              "laplace32": leg_laplace32, "serve_sweep": leg_serve_sweep}[leg]
+              "laplace32": leg_laplace32, "serve_sweep": leg_serve_sweep, "selfconv": leg_selfconv}[leg]
         try:
             extra[leg] = fn(args, dev)
         except Exception as e:  # report, do not lose the main line

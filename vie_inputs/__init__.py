@@ -104,6 +104,19 @@ def grid_coords(n: int, lo: float, hi: float):
     return t[:, None, None], t[None, :, None], t[None, None, :]
 
 
+def nested_nodes(n_coarse: int, n_fine: int) -> slice:
+    """Per-axis slice of an n_fine grid that picks the nodes of the n_coarse grid.
+
+    Cell-centred grids nest only for an odd ratio r = n_fine / n_coarse: coarse
+    node i, at lo + (i + 1/2) D / n_coarse, is fine node r i + (r - 1) / 2.  Used
+    to compare solutions on two grids (a self-convergence study) without
+    interpolation."""
+    r = n_fine // n_coarse if n_coarse >= 1 else 0
+    if r < 1 or r * n_coarse != n_fine or r % 2 == 0:
+        raise ValueError(f"grids {n_coarse} and {n_fine} do not nest (need an odd integer ratio)")
+    return slice((r - 1) // 2, None, r)
+
+
 def _tensor_field(weight: np.ndarray, mat: np.ndarray) -> np.ndarray:
     """weight (n,n,n) real times a constant 3x3 matrix -> (3,3,n,n,n)."""
     return mat.astype(np.complex128)[:, :, None, None, None] * weight[None, None]
