@@ -105,7 +105,9 @@ typedef struct {
  *   kind   vie_kind.
  *   n      points per axis, n = 2^a 3^b 5^c 7^d 11^e with 4 <= n <= 256 (register-
  *          resident kernels for 2n in {64, 96, 128, 192, 256, 384, 512}, shared-
- *          memory Stockham kernels for the other sizes).
+ *          memory Stockham kernels for the other sizes).  Odd n is valid: the
+ *          oversampled set-up grid 3n is then odd and its frequency cut-off is
+ *          the symmetric |m| <= (3n-1)/2, with no Nyquist entry.
  *   lo, hi box [lo, hi]^3 (hi > lo).
  *   omega  angular frequency (ignored for Laplace; >= 0).
  *   eps    device, FP64 complex [9][n][n][n], the 3x3 tensor row-major per node;

@@ -13,7 +13,8 @@ The paper gives no further detail; the readings fixed here are:
 * Oversampling s = 3 (s D >= D + L needs s >= 1 + sqrt 3): the truncated
   kernel is expanded in a Fourier series of period sD, whose periodic images
   cannot reach the box, and the series is cut at |m_a| <= sn/2 (the grid
-  Nyquist frequency pi/h).
+  Nyquist frequency pi/h).  For odd n (odd sn) the cut set is the symmetric
+  |m_a| <= (sn-1)/2, which has no Nyquist entry.
 * For a Fourier symbol S(k) in {1, i k_a, -k_a k_b} the discrete kernel on
   node offsets d in [-(n-1), n-1]^3 is
 
@@ -86,12 +87,16 @@ class Grid:
 
 
 def _axis_wavenumbers(grid: Grid):
-    """k along one axis in FFT order for m in [-sn/2, sn/2); also k with the Nyquist entry zeroed."""
+    """k along one axis in FFT order for the cutoff set of m; also k with the Nyquist entry zeroed.
+
+    Even sn: m in [-sn/2, sn/2), and m = -sn/2 is the Nyquist entry.  Odd sn (odd n):
+    m in [-(sn-1)/2, (sn-1)/2], symmetric, with no Nyquist entry to treat."""
     sn = grid.sn
-    m = np.fft.fftfreq(sn, d=1.0 / sn)  # 0..sn/2-1, -sn/2..-1
+    m = np.fft.fftfreq(sn, d=1.0 / sn)  # even sn: 0..sn/2-1, -sn/2..-1; odd sn: 0..(sn-1)/2, -(sn-1)/2..-1
     k = 2.0 * np.pi * m / (OVERSAMPLE * grid.D)
     k_odd = k.copy()
-    k_odd[sn // 2] = 0.0  # mean of S at k_a = -pi/h and +pi/h for odd factors
+    if sn % 2 == 0:
+        k_odd[sn // 2] = 0.0  # mean of S at k_a = -pi/h and +pi/h for odd factors
     return k, k_odd
 
 

@@ -155,22 +155,25 @@ __global__ void k_ghat_table(double2* tab, int jmax, double dk, double w, double
   tab[j] = dev_ghat(dk * sqrt((double)j), w, L);
 }
 
-// F(m) = S~(k_m) G^(|k_m|) on the (sn)^3 grid in FFT order; Nyquist rule: on an
-// axis with m_a = -sn/2 an odd factor k_a is replaced by 0 (the mean of its
-// values at -pi/h and +pi/h), an even factor k_a^2 is kept.
+// F(m) = S~(k_m) G^(|k_m|) on the (sn)^3 grid in FFT order.  Even sn: m in
+// [-sn/2, sn/2), and on an axis with m_a = -sn/2 (Nyquist) an odd factor k_a is
+// replaced by 0 (the mean of its values at -pi/h and +pi/h), an even factor k_a^2
+// is kept.  Odd sn (odd n): m in [-(sn-1)/2, (sn-1)/2], no Nyquist entry.  Either
+// way |m_a| <= sn/2 (integer division), so m.m <= 3 (sn/2)^2, the table's length.
 __global__ void k_build_F(double2* __restrict__ F, const double2* __restrict__ tab, int sn, int sym, double dk) {
   const long long tot = (long long)sn * sn * sn;
+  const int hp = (sn + 1) / 2;                // first index of a negative m
+  const int nyq = (sn % 2 == 0) ? sn / 2 : -1;  // index of m = -sn/2, if any
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(idx % sn);
     const int iy = (int)((idx / sn) % sn);
     const int iz = (int)(idx / ((long long)sn * sn));
-    const int h = sn / 2;
-    const int mx = ix < h ? ix : ix - sn, my = iy < h ? iy : iy - sn, mz = iz < h ? iz : iz - sn;
+    const int mx = ix < hp ? ix : ix - sn, my = iy < hp ? iy : iy - sn, mz = iz < hp ? iz : iz - sn;
     const long long j = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
     const double2 G = tab[j];
     const double kx = dk * mx, ky = dk * my, kz = dk * mz;
-    const double ox = (ix == h) ? 0.0 : kx, oy = (iy == h) ? 0.0 : ky, oz = (iz == h) ? 0.0 : kz;
+    const double ox = (ix == nyq) ? 0.0 : kx, oy = (iy == nyq) ? 0.0 : ky, oz = (iz == nyq) ? 0.0 : kz;
     double2 v;
     switch (sym) {
       case SYM_1: v = G; break;

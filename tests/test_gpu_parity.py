@@ -444,6 +444,42 @@ def test_radix_5_7_11_sizes(vie, kind, n):
     P.close()
 
 
+@pytest.mark.parametrize("kind,n,mu", [("laplace", 5, False), ("helmholtz", 9, False), ("maxwell", 15, True),
+                                       ("helmholtz", 21, False)])
+def test_odd_grid_sizes(vie, kind, n, mu):
+    """Odd n: the oversampled set-up grid 3n is odd (a symmetric frequency cut with no
+    Nyquist entry), and the n^2 x-lines leave the last tile of the generic x passes
+    partly empty.  FP64, double-word and FP32 applies and an FP64 solve against the oracle."""
+    import torch
+
+    p = make_problem(kind, n, 2.0, mu, seed=7)
+    P = vie.Problem(kind, n, p.lo, p.hi, p.omega, eps_dev(p), mu_dev(p))
+    try:
+        op = operators.OracleProblem.from_problem(p)
+        x = vi.random_field(n, op.ncomp, 13)[0]
+        for prec, dt, tol in ((vie.VIE_FP64, torch.complex128, 1e-12), (vie.VIE_DF64, torch.complex128, 1e-12),
+                              (vie.VIE_FP32, torch.complex64, 2e-5)):
+            xd = to_dev(x, dt)
+            yd = torch.empty_like(xd)
+            P.apply(xd, yd, prec)
+            torch.cuda.synchronize()
+            ref = op.apply(x if dt == torch.complex128 else x.astype(np.complex64).astype(np.complex128))
+            assert rel(yd.cpu().numpy(), ref) <= tol, prec
+        d = p.directions[0]
+        pol = p.polarisations[0] if kind == "maxwell" else None
+        b = torch.empty((op.ncomp, n, n, n), dtype=torch.complex128, device="cuda:0")
+        P.rhs(d, pol, 1, b)
+        bo = op.rhs(d, pol)
+        assert rel(b.cpu().numpy(), bo) <= 1e-12
+        J = torch.zeros_like(b)
+        st, info = P.solve(b, J, tol=1e-11, restart=60)
+        Jo, _ = solvers.gmres(op.apply, bo, tol=1e-13, restart=60)
+        assert info.rel_residual <= 1e-11
+        assert rel(J.cpu().numpy(), Jo) <= 1e-9
+    finally:
+        P.close()
+
+
 @pytest.mark.parametrize("medium,kind", [("eps234", "helmholtz"), ("eps_dense", "maxwell")])
 def test_bicgstab_matches_oracle_on_paper_media(vie, medium, kind):
     """The paper's solver (Sec. 5) on its media (Sec. 5.2): same solution and matvec count as the oracle."""

@@ -28,9 +28,9 @@ def gaussian(grid):
     return (ALPHA / np.pi) ** 1.5 * np.exp(-ALPHA * r2), np.sqrt(r2)
 
 
-@pytest.mark.parametrize("omega", [0.0, 3.7])
-def test_fft_kernels_equal_direct_sum(omega):
-    g = discrete.Grid(8)
+@pytest.mark.parametrize("n,omega", [(8, 0.0), (8, 3.7), (5, 3.7)])
+def test_fft_kernels_equal_direct_sum(n, omega):
+    g = discrete.Grid(n)
     src, dst, d = discrete._offset_indices(g)
     n = g.n
     for name in discrete.SYMBOLS:
@@ -66,6 +66,31 @@ def test_kernel_direct_single_term_loop():
     assert abs(got - acc) <= 1e-14 * max(1.0, abs(acc))
 
 
+def test_kernel_direct_single_term_loop_odd_grid():
+    """Odd n: the oversampled grid sn = 3n is odd, the cut set |m_a| <= (sn-1)/2 is
+    symmetric and has no Nyquist entry, so every odd factor k_a is kept."""
+    g = discrete.Grid(3)
+    sn = g.sn
+    omega = 1.3
+    from oracle.greens import truncated_green_hat
+
+    for name, d in (("xy", (1, -2, 2)), ("dx", (0, 1, -2))):
+        kd = discrete.kernel_direct(name, g, omega)
+        acc = 0j
+        half = (sn - 1) // 2
+        for mz in range(-half, half + 1):
+            for my in range(-half, half + 1):
+                for mx in range(-half, half + 1):
+                    kz, ky, kx = (2 * np.pi * m / (3 * g.D) for m in (mz, my, mx))
+                    kap = math.sqrt(kx * kx + ky * ky + kz * kz)
+                    G = truncated_green_hat(np.array([kap]), omega, g.L)[0]
+                    S = -kx * ky if name == "xy" else 1j * kx
+                    acc += S * G * np.exp(2j * np.pi * (mz * d[0] + my * d[1] + mx * d[2]) / sn)
+        acc /= sn ** 3
+        got = kd[d[0] + 2, d[1] + 2, d[2] + 2]
+        assert abs(got - acc) <= 1e-14 * max(1.0, abs(acc)), name
+
+
 @pytest.mark.parametrize("name", ["1", "dx", "xx", "xz", "yz"])
 def test_fft_convolution_equals_toeplitz(name):
     g = discrete.Grid(8)
@@ -77,8 +102,9 @@ def test_fft_convolution_equals_toeplitz(name):
     assert np.linalg.norm(y1 - y2) <= 1e-14 * np.linalg.norm(y2) * 10
 
 
-def test_kernel_parity_and_reality():
-    g = discrete.Grid(8)
+@pytest.mark.parametrize("n", [8, 5])
+def test_kernel_parity_and_reality(n):
+    g = discrete.Grid(n)
     n = g.n
     idx = (-np.arange(2 * n)) % (2 * n)
     for omega in (0.0, 2.0):
