@@ -125,7 +125,8 @@ int vie_problem_ncomp(const vie_problem* P);
 
 /* y = (I + B + K) x, the left-hand side of Eq. (eq:intLap), (eq:intH) or (eq:intM).
  *   x, y   device, [nrhs][c][n][n][n], FP64 complex (precision VIE_FP64 or
- *          VIE_DF64) or FP32 complex (VIE_FP32); x and y must not overlap.
+ *          VIE_DF64) or FP32 complex (VIE_FP32); x and y must not share a byte
+ *          (VIE_EINVAL).
  *   nrhs   >= 1.  Asynchronous on stream.  The first VIE_DF64 apply of a
  *   handle converts its tables to double-word form (device memory of the size
  *   of the FP64 kernel and medium tables, kept until destroy). */
@@ -168,7 +169,8 @@ vie_status vie_rhs_plane_wave(vie_problem* P, const double* d, const double* p, 
 /* Solve (I + B + K) J = rhs by restarted GMRES (Sec. 1 and Sec. 6 name GMRES for
  * these second-kind equations).
  *   rhs  device, FP64 complex [nrhs][c][n][n][n].
- *   J    device, same layout: initial guess on entry (zeros for none), solution on exit.
+ *   J    device, same layout: initial guess on entry (zeros for none), solution on
+ *        exit; must not overlap rhs (VIE_EINVAL).
  *   opt  solver options (nrhs from opt->nrhs); info may be NULL.
  * Synchronises the stream.  Returns VIE_ENOCONV (J holds the last iterate) if a
  * right-hand side misses the tolerance, VIE_ENAN on non-finite residuals. */
@@ -180,7 +182,7 @@ vie_status vie_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_o
  *     summary after Eq. (eq:intH)); field_out [nrhs][1][n][n][n].
  *   Maxwell: [E_sc; H_sc] by Eq. (represent_Maxwell) (or Eq.
  *     (represent_Maxwell_reduced) when mu = I); field_out [nrhs][6][n][n][n].
- * Asynchronous on stream. */
+ * J and field_out must not overlap (VIE_EINVAL).  Asynchronous on stream. */
 vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, int nrhs, void* stream);
 
 /* Device bytes a problem of this shape holds (medium, kernels, apply workspace

@@ -51,8 +51,13 @@ using namespace vie;
 
 extern "C" vie_status vie_apply_static(vie_problem* P, const void* x, void* y, int precision, int nrhs,
                                        void* stream) {
-  if (!P || !x || !y || nrhs < 1 || (precision != VIE_FP64 && precision != VIE_FP32) || x == y) {
+  if (!P || !x || !y || nrhs < 1 || (precision != VIE_FP64 && precision != VIE_FP32)) {
     set_error("vie_apply_static: bad argument");
+    return VIE_EINVAL;
+  }
+  const size_t vb = grid_vec_bytes(P, P->ncomp, nrhs, precision == VIE_FP32 ? sizeof(float2) : sizeof(double2));
+  if (ranges_overlap(x, vb, y, vb)) {
+    set_error("vie_apply_static: x and y must not overlap");
     return VIE_EINVAL;
   }
   const KernelSet& K = P->kapply;

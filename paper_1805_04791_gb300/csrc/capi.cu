@@ -27,6 +27,15 @@ vie_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_ECUDA;
 }
 
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+size_t grid_vec_bytes(const vie_problem* P, int c, int nrhs, size_t elem) {
+  return elem * (size_t)nrhs * (size_t)c * (size_t)P->n * (size_t)P->n * (size_t)P->n;
+}
+
 // Grid sizes whose 2n and 3n transforms factor into the codelet radices.
 static bool smooth_size(int n) {
   if (n < 4 || n > 256) return false;
@@ -141,7 +150,8 @@ vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int 
     set_error("vie_apply: bad argument");
     return VIE_EINVAL;
   }
-  if (x == y) {
+  const size_t vb = grid_vec_bytes(P, P->ncomp, nrhs, precision == VIE_FP32 ? sizeof(float2) : sizeof(double2));
+  if (ranges_overlap(x, vb, y, vb)) {
     set_error("vie_apply: x and y must not overlap");
     return VIE_EINVAL;
   }
@@ -166,12 +176,22 @@ vie_status vie_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_o
     set_error("vie_solve: bad argument");
     return VIE_EINVAL;
   }
+  const size_t vb = grid_vec_bytes(P, P->ncomp, opt->nrhs, sizeof(double2));
+  if (ranges_overlap(rhs, vb, J, vb)) {
+    set_error("vie_solve: rhs and J must not overlap");
+    return VIE_EINVAL;
+  }
   return run_solve(P, rhs, J, opt, info, (cudaStream_t)stream);
 }
 
 vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, int nrhs, void* stream) {
   if (!P || !J || !field_out || nrhs < 1) {
     set_error("vie_eval_scattered: bad argument");
+    return VIE_EINVAL;
+  }
+  if (ranges_overlap(J, grid_vec_bytes(P, P->ncomp, nrhs, sizeof(double2)), field_out,
+                     grid_vec_bytes(P, P->kind == VIE_MAXWELL ? 6 : 1, nrhs, sizeof(double2)))) {
+    set_error("vie_eval_scattered: J and field_out must not overlap");
     return VIE_EINVAL;
   }
   vie_status s = build_eval_kernels(P, (cudaStream_t)stream);

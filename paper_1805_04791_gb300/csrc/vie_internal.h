@@ -100,6 +100,10 @@ void set_error(const std::string& msg);
 cudaError_t dalloc(void** p, size_t bytes, cudaStream_t st);
 void dfree(void* p, cudaStream_t st);
 vie_status cuda_fail(cudaError_t e, const char* what);
+// Whether the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb);
+// Bytes of nrhs vectors of c components on the problem's grid, elem bytes per value.
+size_t grid_vec_bytes(const vie_problem* P, int c, int nrhs, size_t elem);
 
 #define VIE_CK(call)                                               \
   do {                                                             \

@@ -203,6 +203,25 @@ def test_invalid_arguments(vie):
         vie.vie_apply(P.handle, x, x, vie.VIE_FP64)
     with pytest.raises(vie.VieError):
         vie.vie_apply(P.handle, x, torch.empty_like(x), 7)
+    # a valid apply first: buffers that touch without sharing a byte are accepted
+    N = 8 ** 3
+    f32 = torch.zeros(2 * 3 * N, dtype=torch.complex64, device="cuda:0")
+    vie.vie_apply(P.handle, f32[:3 * N].view(3, 8, 8, 8), f32[3 * N:].view(3, 8, 8, 8), vie.VIE_FP32)  # adjacent
+    y = torch.empty_like(x)
+    vie.vie_apply(P.handle, x, y, vie.VIE_FP64)
+    torch.cuda.synchronize()
+    # views one element apart share all but one element: every entry point refuses them
+    buf = torch.zeros(3 * N + 1, dtype=torch.complex128, device="cuda:0")
+    a, b = buf[:3 * N].view(3, 8, 8, 8), buf[1:].view(3, 8, 8, 8)
+    for call in (lambda: vie.vie_apply(P.handle, a, b, vie.VIE_FP64),
+                 lambda: vie.vie_solve(P.handle, a, b, vie.SolveOpts(1e-10, 20, 5, 100, 1e-5, vie.VIE_SOLVE_FP64, 1)),
+                 lambda: vie.vie_eval_scattered(P.handle, a, buf[2 * N:3 * N].view(1, 8, 8, 8)),
+                 # FP32 vectors: 8 bytes per value
+                 lambda: vie.vie_apply(P.handle, f32[:3 * N].view(3, 8, 8, 8),
+                                       f32[3 * N - 1:6 * N - 1].view(3, 8, 8, 8), vie.VIE_FP32)):
+        with pytest.raises(vie.VieError) as ei:
+            call()
+        assert ei.value.status == vie.VIE_EINVAL
 
 
 def test_smallest_grid_and_zero_input(vie):

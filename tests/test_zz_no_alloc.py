@@ -65,4 +65,9 @@ def test_static_apply_rejects_oversize_and_untuned(vie):
     assert ei.value.status == vie.VIE_EINVAL
     Q.tune(vie.VIE_FP64)
     vie.vie_apply_static(Q.handle, x, torch.empty_like(x), vie.VIE_FP64)
+    N = 32 ** 3
+    buf = torch.zeros(3 * N + 1, dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(vie.VieError) as ei:  # x and y one element apart share all but one element
+        vie.vie_apply_static(Q.handle, buf[1:].view(3, 32, 32, 32), buf[:3 * N].view(3, 32, 32, 32), vie.VIE_FP64)
+    assert ei.value.status == vie.VIE_EINVAL
     Q.close()
