@@ -121,6 +121,52 @@ def test_scattered_field(vie, case):
     assert rel(out.cpu().numpy(), op.scattered(x)) <= 1e-12
 
 
+@pytest.mark.parametrize("case", [("laplace", 32, 0.0, False), ("helmholtz", 24, 4.0, False),
+                                  ("maxwell", 16, 3.0, True)], ids=lambda c: f"{c[0]}-{c[1]}-mu{int(c[3])}")
+def test_scattered_field_batched_equals_single(vie, case):
+    """Two densities in one vie_eval_scattered call give, bit for bit, the fields of two
+    single calls (n = 32 runs the register-resident kernels, 24 and 16 the generic ones)."""
+    import torch
+
+    p, P, op = setup(vie, *case)
+    x = vi.random_field(p.n, op.ncomp, 5, nrhs=2)
+    cout = 1 if p.kind != "maxwell" else 6
+    xd = to_dev(x)
+    out = torch.empty((2, cout, p.n, p.n, p.n), dtype=torch.complex128, device="cuda:0")
+    P.eval_scattered(xd, out, nrhs=2)
+    for r in range(2):
+        single = torch.empty_like(out[r])
+        P.eval_scattered(xd[r].contiguous(), single)
+        torch.cuda.synchronize()
+        assert torch.equal(single, out[r])
+    assert rel(out[1].cpu().numpy(), op.scattered(x[1])) <= 1e-12
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "bicgstab"])
+def test_solve_from_nonzero_initial_guess(vie, mode):
+    """A non-zero initial guess -- the solution perturbed by 1e-3, and a random vector
+    ten times its size -- converges to the oracle's solution; the near guess takes
+    fewer applies than a zero start (its residual is computed, not assumed to be b)."""
+    import torch
+
+    p, P, op = setup(vie, "helmholtz", 24, 4.0, False)
+    m = {"fp64": vie.VIE_SOLVE_FP64, "mixed": vie.VIE_SOLVE_MIXED, "bicgstab": vie.VIE_SOLVE_BICGSTAB}[mode]
+    d = p.directions[0]
+    b = torch.empty((3, 24, 24, 24), dtype=torch.complex128, device="cuda:0")
+    P.rhs(d, None, 1, b)
+    Jo, _ = solvers.gmres(op.apply, op.rhs(d), tol=1e-13, restart=60)
+    noise = vi.random_field(24, 3, 17)[0]
+    scale = np.linalg.norm(Jo) / np.linalg.norm(noise)
+    applies = []
+    for J0 in (np.zeros_like(Jo), Jo + 1e-3 * scale * noise, 10 * scale * noise):
+        J = to_dev(J0)
+        st, info = P.solve(b, J, tol=1e-10, restart=40, mode=m, max_outer=30, max_inner=2000)
+        assert info.rel_residual <= 1e-10
+        assert rel(J.cpu().numpy(), Jo) <= 1e-8
+        applies.append(info.applies_fp32 + info.applies_fp64)
+    assert applies[1] < applies[0]
+
+
 def test_solve_fp64_laplace_32(vie):
     """Config-1 workload: anisotropic Laplace bump, 32^3, GMRES to 1e-10 (FP64)."""
     import torch
