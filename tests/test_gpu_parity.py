@@ -142,6 +142,40 @@ def test_scattered_field_batched_equals_single(vie, case):
     assert rel(out[1].cpu().numpy(), op.scattered(x[1])) <= 1e-12
 
 
+@pytest.mark.parametrize("kind,n", [("laplace", 12), ("helmholtz", 32), ("maxwell", 16)])
+def test_vacuum_operator_is_identity(vie, kind, n):
+    """No scatterer (eps = I, and mu = I given explicitly for Maxwell): H = 0, so the
+    apply returns its input (exactly in FP64 and FP32; the double-word form holds ~48
+    bits), the right-hand side is zero and the solve returns J = 0.  n = 32 runs the
+    register-resident kernels."""
+    import torch
+
+    eye = to_dev(vi.identity_field(n).reshape(9, -1))
+    P = vie.Problem(kind, n, -1.0, 1.0, 0.0 if kind == "laplace" else 2.0, eye, eye if kind == "maxwell" else None)
+    try:
+        c = P.ncomp
+        x = vi.random_field(n, c, 19)[0]
+        for prec, dt in ((vie.VIE_FP64, torch.complex128), (vie.VIE_FP32, torch.complex64),
+                         (vie.VIE_DF64, torch.complex128)):
+            xd = to_dev(x, dt)
+            yd = torch.empty_like(xd)
+            P.apply(xd, yd, prec)
+            torch.cuda.synchronize()
+            if prec == vie.VIE_DF64:
+                assert rel(yd.cpu().numpy(), x) <= 1e-14
+            else:
+                assert torch.equal(yd, xd), prec
+        b = torch.empty((c, n, n, n), dtype=torch.complex128, device="cuda:0")
+        P.rhs(np.array([0.0, 0.6, 0.8]), np.array([1.0, 0.0, 0.0]) if kind == "maxwell" else None, 1, b)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(b) == 0
+        J = torch.ones_like(b)
+        P.solve(b, J)
+        assert torch.count_nonzero(J) == 0
+    finally:
+        P.close()
+
+
 @pytest.mark.parametrize("mode", ["fp64", "mixed", "bicgstab"])
 def test_solve_from_nonzero_initial_guess(vie, mode):
     """A non-zero initial guess -- the solution perturbed by 1e-3, and a random vector

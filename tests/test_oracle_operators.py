@@ -116,6 +116,20 @@ def test_maxwell_mu_identity_reduces():
     assert nrm(x6[:3] - x3) <= 1e-11 * nrm(x3)
 
 
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz", "maxwell"])
+def test_vacuum_operator_is_identity(kind):
+    """No scatterer (eps = mu = I): H = 0 (Eq. (rhodef)), so B and K vanish and the
+    operator is exactly the identity; the right-hand side is zero and so is J."""
+    n = 6
+    eye = vi.identity_field(n)
+    op = operators.OracleProblem(kind, n, -1.0, 1.0, 0.0 if kind == "laplace" else 2.0, eye,
+                                 eye if kind == "maxwell" else None)
+    x = vi.random_field(n, op.ncomp, 11)[0]
+    assert np.array_equal(op.apply(x), x)
+    b = op.rhs(np.array([0.0, 0.6, 0.8]), np.array([1.0, 0.0, 0.0]) if kind == "maxwell" else None)
+    assert np.max(np.abs(b)) == 0.0
+
+
 def test_maxwell_low_frequency_is_laplace():
     n = 6
     pm = vi.maxwell_problem(n=n, wavelengths=1e-10, with_mu=False)
