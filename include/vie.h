@@ -38,6 +38,22 @@
  *   so calls on other handles and streams are never serialised by it; the
  *   stream given to vie_problem_create must stay valid until
  *   vie_problem_destroy, which frees on it.
+ *
+ * Environment variables (read at each call; for testing and measurement --
+ * none is needed in normal use)
+ * --------------------------------------------------------------------------
+ * - VIE_P3_VARIANT=k    every register-resident apply runs z-pass variant k
+ *                       (see vie_tune), bypassing the process-wide tuning
+ *                       cache; shapes k does not fit return VIE_EINVAL.
+ * - VIE_TUNE=0          vie_tune takes the first applicable variant untimed.
+ * - VIE_GENERIC_FFT     (set to any value) the generic shared-memory kernels
+ *                       run at every size, also where register-resident ones exist.
+ * - VIE_GROUP_MAX=g     batched solves use lockstep groups of at most g
+ *                       right-hand sides (default: from free device memory, <= 64).
+ * - VIE_RESIDUAL_FP64=1 mixed solves compute their residuals with the native
+ *                       FP64 apply instead of the double-word one.
+ * - VIE_SETUP_FP64=1    the set-up's kernel-transform FFTs run in native FP64
+ *                       instead of double-word arithmetic.
  */
 #ifndef VIE_H
 #define VIE_H
