@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--case", default=None, choices=["apply"],
                     help="minimal run for profilers: build the problem, run --reps FP32 applies, exit")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df64"],
+                    help="precision of the --case apply run")
     return ap.parse_args()
 
 
@@ -748,10 +750,12 @@ def run_case(args):
     n = args.n
     p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
     P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev))
-    x = torch.randn((3, n, n, n), dtype=torch.complex64, device=dev)
+    prec = {"fp32": vie.VIE_FP32, "fp64": vie.VIE_FP64, "df64": vie.VIE_DF64}[args.prec]
+    dt = torch.complex64 if args.prec == "fp32" else torch.complex128
+    x = torch.randn((3, n, n, n), dtype=dt, device=dev)
     y = torch.empty_like(x)
     for _ in range(args.reps):
-        P.apply(x, y, vie.VIE_FP32)
+        P.apply(x, y, prec)
     torch.cuda.synchronize()
     P.close()
     print("case ok")
