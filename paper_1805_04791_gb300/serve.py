@@ -86,6 +86,7 @@ class Server:
 
         import vie_inputs as vi
 
+        P = None
         try:
             torch.cuda.set_device(self.device)
             stream = torch.cuda.Stream()
@@ -107,11 +108,18 @@ class Server:
                 if self.keep:
                     res.solution = J.cpu().numpy()
                 res.status = "ok" if st == 0 else "noconv"
-                P.close()
                 del eps, b, J
         except Exception as e:  # a failed request frees its slot and is reported
             res.status = f"error: {e}"
         finally:
+            # the handle's device memory goes back before the slot does (destroy
+            # frees stream-ordered on the handle's stream and waits for it)
+            if P is not None:
+                try:
+                    P.close()
+                except Exception as e:
+                    if res.status == "ok":
+                        res.status = f"error: {e}"
             done_cb(res)
 
     def run(self, requests, time_scale: float = 1.0) -> ServeStats:

@@ -96,3 +96,46 @@ def test_oversized_request_is_rejected_not_hung():
     for r in stats.results:
         big = r.n * 1000 > 100_000
         assert (r.status.startswith("rejected")) == big
+
+
+def test_failed_request_releases_its_problem(monkeypatch):
+    """A request whose solve raises is reported as an error, its problem handle is
+    closed (its device memory returns before its slot does) and the slot is freed."""
+    torch = pytest.importorskip("torch")
+    import contextlib
+
+    from paper_1805_04791_gb300 import serve
+
+    closed = []
+
+    class FakeProblem:
+        def __init__(self, kind, n, lo, hi, omega, eps, mu=None, stream=None):
+            self.ncomp = 3
+
+        def rhs(self, *a, **k):
+            pass
+
+        def solve(self, *a, **k):
+            raise RuntimeError("solver failed")
+
+        def close(self):
+            closed.append(True)
+
+    class FakeStream:
+        def synchronize(self):
+            pass
+
+    monkeypatch.setattr(serve, "Problem", FakeProblem)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(vi, "bump_medium_torch", lambda n, seed, dev: torch.zeros(9, n ** 3, dtype=torch.complex128))
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, **k: real_empty(*a, **{**k, "device": "cpu"}))
+    req = vi.serving_mix(1, rate_per_s=10.0, seed=4)[0]
+    res = serve.ServeResult(req.rid, req.kind, 8, 0.0)
+    req.n = 8
+    done = []
+    serve.Server()._solve(req, res, done.append)
+    assert res.status == "error: solver failed"
+    assert closed == [True] and done == [res]
