@@ -5,6 +5,9 @@ only: every step of the computation runs in the library's CUDA kernels).
 Functions carry the C names; ``Problem`` is a small convenience wrapper.
 PyTorch provides device memory and streams: tensors are passed by
 ``data_ptr()`` and the stream by ``torch.cuda.current_stream().cuda_stream``.
+Each tensor is checked before the call (a contiguous CUDA tensor with at least
+the bytes the call's sizes imply), so a short, strided or host buffer is refused
+with VIE_EINVAL instead of being accessed out of bounds by the kernels.
 
 There is no CPU fallback: if the shared library is missing or fails to load,
 importing the binding raises.
@@ -110,8 +113,43 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+# (n, components, kind) of every handle created through this binding: lets the
+# calls below check that each tensor they hand to the library is big enough.
+_SHAPES = {}
+
+
+def _key(P):
+    return P.value if isinstance(P, ctypes.c_void_p) else P
+
+
+def _dev(t, need_bytes, what):
+    """Device pointer of ``t``, refused (VIE_EINVAL, nothing launched) unless ``t`` is a
+    contiguous CUDA tensor holding at least ``need_bytes`` bytes (None: size unknown).
+    The library reads and writes exactly the bytes the call's sizes imply, so a
+    smaller, strided or host buffer would be accessed out of bounds."""
+    if t is None or not hasattr(t, "data_ptr"):
+        raise VieError(VIE_EINVAL, f"{what}: expected a CUDA tensor")
+    if not t.is_cuda:
+        raise VieError(VIE_EINVAL, f"{what}: expected a CUDA tensor, got one on {t.device}")
+    if not t.is_contiguous():
+        raise VieError(VIE_EINVAL, f"{what}: expected a contiguous tensor")
+    have = t.numel() * t.element_size()
+    if need_bytes is not None and have < need_bytes:
+        raise VieError(VIE_EINVAL, f"{what}: holds {have} bytes, the call accesses {need_bytes}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _vec_bytes(P, comps, nrhs, elem):
+    """Bytes of nrhs fields of ``comps`` components on P's grid (None if P is unknown)."""
+    sh = _SHAPES.get(_key(P))
+    if sh is None:
+        return None
+    c = sh[1] if comps is None else comps(sh)
+    return elem * max(nrhs, 0) * c * sh[0] ** 3
+
+
+def _elem(precision):
+    return 8 if precision == VIE_FP32 else 16
 
 
 def _dvec(values):
@@ -125,8 +163,12 @@ def _dvec(values):
 
 
 def vie_problem_create(kind: int, n: int, lo: float, hi: float, omega: float, eps, mu=None, stream=None):
+    need = 16 * 9 * max(n, 0) ** 3
+    pe = _dev(eps, need, "eps")
+    pm = None if mu is None else _dev(mu, need, "mu")
     h = ctypes.c_void_p()
-    _check(load().vie_problem_create(kind, n, lo, hi, omega, _ptr(eps), _ptr(mu), _stream(stream), ctypes.byref(h)))
+    _check(load().vie_problem_create(kind, n, lo, hi, omega, pe, pm, _stream(stream), ctypes.byref(h)))
+    _SHAPES[h.value] = (n, load().vie_problem_ncomp(h), kind)
     return h
 
 
@@ -135,29 +177,40 @@ def vie_problem_ncomp(P) -> int:
 
 
 def vie_apply(P, x, y, precision: int, nrhs: int = 1, stream=None):
-    return _check(load().vie_apply(P, _ptr(x), _ptr(y), precision, nrhs, _stream(stream)))
+    need = _vec_bytes(P, None, nrhs, _elem(precision))
+    px, py = _dev(x, need, "x"), _dev(y, need, "y")
+    return _check(load().vie_apply(P, px, py, precision, nrhs, _stream(stream)))
 
 
 def vie_apply_static(P, x, y, precision: int, nrhs: int = 1, stream=None):
     """vie_apply with the scratch in the library's fixed device array (allocates nothing)."""
-    return _check(load().vie_apply_static(P, _ptr(x), _ptr(y), precision, nrhs, _stream(stream)))
+    need = _vec_bytes(P, None, nrhs, _elem(precision))
+    px, py = _dev(x, need, "x"), _dev(y, need, "y")
+    return _check(load().vie_apply_static(P, px, py, precision, nrhs, _stream(stream)))
 
 
 def vie_rhs_plane_wave(P, d, p, nrhs: int, rhs_out, stream=None):
+    dd = _dvec(d)
     pp = None if p is None else _dvec(p)
-    return _check(load().vie_rhs_plane_wave(P, _dvec(d), pp, nrhs, _ptr(rhs_out), _stream(stream)))
+    if len(dd) < 3 * nrhs or (pp is not None and len(pp) < 3 * nrhs):
+        raise VieError(VIE_EINVAL, "vie_rhs_plane_wave: d and p need 3 values per right-hand side")
+    out = _dev(rhs_out, _vec_bytes(P, None, nrhs, 16), "rhs_out")
+    return _check(load().vie_rhs_plane_wave(P, dd, pp, nrhs, out, _stream(stream)))
 
 
 def vie_solve(P, rhs, J, opts: SolveOpts, stream=None, allow_noconv=False):
     info = SolveInfo()
     allow = (VIE_OK, VIE_ENOCONV) if allow_noconv else (VIE_OK,)
-    st = _check(load().vie_solve(P, _ptr(rhs), _ptr(J), ctypes.byref(opts), ctypes.byref(info), _stream(stream)),
-                allow)
+    need = _vec_bytes(P, None, opts.nrhs, 16)
+    pr, pj = _dev(rhs, need, "rhs"), _dev(J, need, "J")
+    st = _check(load().vie_solve(P, pr, pj, ctypes.byref(opts), ctypes.byref(info), _stream(stream)), allow)
     return st, info
 
 
 def vie_eval_scattered(P, J, field_out, nrhs: int = 1, stream=None):
-    return _check(load().vie_eval_scattered(P, _ptr(J), _ptr(field_out), nrhs, _stream(stream)))
+    pj = _dev(J, _vec_bytes(P, None, nrhs, 16), "J")
+    po = _dev(field_out, _vec_bytes(P, lambda sh: 6 if sh[2] == VIE_MAXWELL else 1, nrhs, 16), "field_out")
+    return _check(load().vie_eval_scattered(P, pj, po, nrhs, _stream(stream)))
 
 
 def vie_problem_bytes(kind: int, n: int, nrhs: int, restart: int, has_mu: int) -> int:
@@ -165,6 +218,7 @@ def vie_problem_bytes(kind: int, n: int, nrhs: int, restart: int, has_mu: int) -
 
 
 def vie_problem_destroy(P):
+    _SHAPES.pop(_key(P), None)
     return _check(load().vie_problem_destroy(P))
 
 
