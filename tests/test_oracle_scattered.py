@@ -1,0 +1,138 @@
+"""Pins for the oracle's scattered fields (Sec. 2 existence proof, the summary after
+Eq. (eq:intH), Eqs. (represent_Maxwell) and (represent_Maxwell_reduced)).
+
+Density: J = p g and M = q g with the normalised Gaussian g(r) = (a/pi)^{3/2}
+exp(-a r^2), resolved on the grid.  Its volume potential u = V_w g is radial; in
+closed form for w = 0 (u = erf(sqrt(a) r) / (4 pi r)), and for w > 0 by the l = 0
+addition theorem with two 1D integrals,
+
+    u(r)  = [e^{iwr} A(r) + sin(wr) B(r)] / (w r),
+    A(r)  = int_0^r g(s) s sin(ws) ds,   B(r) = int_r^inf g(s) s e^{iws} ds,
+    u'(r) = -u / r + [i e^{iwr} A(r) + cos(wr) B(r)] / r,
+    u''   = -g - 2 u' / r - w^2 u           (the radial Helmholtz equation).
+
+With x^ = x / r and Hess u = u'' x^ x^T + (u' / r)(I - x^ x^T):
+
+    div V J           = u' (p . x^),
+    grad div V J      = (Hess u) p,
+    curl V J          = u' (x^ x p),
+
+so the fields of the representations follow without any 3D machinery:
+
+    reduced Maxwell   E = (Hess u) p + w^2 u p,       H = -i w u' (x^ x p),
+    Maxwell [J; M]    E = (Hess u) p + w^2 u p + i w u' (x^ x q),
+                      H = (Hess u) q + w^2 u q - i w u' (x^ x p).
+
+A dropped term, a flipped sign of the i w curl terms or a swapped J / M fails these.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+from scipy import integrate
+
+from oracle import discrete, operators
+
+ALPHA = 36.0
+N = 48
+P_VEC = np.array([0.3, -0.5, 0.8])
+Q_VEC = np.array([-0.6, 0.2, 0.4])
+
+
+def g_of(r):
+    return (ALPHA / np.pi) ** 1.5 * np.exp(-ALPHA * r * r)
+
+
+def radial_u(r, omega):
+    """u, u', u'' of V_w g at radius r > 0."""
+    if omega == 0.0:
+        u = sp.erf(math.sqrt(ALPHA) * r) / (4 * np.pi * r)
+        up = (2 * math.sqrt(ALPHA / np.pi) * r * math.exp(-ALPHA * r * r) - sp.erf(math.sqrt(ALPHA) * r)) / (
+            4 * np.pi * r * r)
+    else:
+        R = 1.5  # g(R) ~ 1e-35
+        q = lambda f, a, b: integrate.quad(f, a, b, epsabs=0, epsrel=1e-13, limit=200)[0]
+        A = q(lambda s: g_of(s) * s * math.sin(omega * s), 0.0, r)
+        B = q(lambda s: g_of(s) * s * math.cos(omega * s), r, R) + 1j * q(lambda s: g_of(s) * s * math.sin(omega * s), r, R)
+        e = np.exp(1j * omega * r)
+        u = (e * A + math.sin(omega * r) * B) / (omega * r)
+        up = -u / r + (1j * e * A + math.cos(omega * r) * B) / r
+    upp = -g_of(r) - 2.0 * up / r - omega * omega * u
+    return u, up, upp
+
+
+def sample_points(grid, count=40, seed=0):
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(N // 4, 3 * N // 4, size=(count, 3))  # where g and its fields are not negligible
+    t = grid.nodes()
+    return idx, np.stack([t[idx[:, 2]], t[idx[:, 1]], t[idx[:, 0]]], -1)  # (x, y, z) of [z, y, x] indices
+
+
+def reference_fields(x, omega, with_m):
+    """phi = div V J, and [E; H] of the chosen representation, at the points x."""
+    phis, Es, Hs = [], [], []
+    for pt in x:
+        r = float(np.linalg.norm(pt))
+        xh = pt / r
+        u, up, upp = radial_u(r, omega)
+        hess = upp * np.outer(xh, xh) + (up / r) * (np.eye(3) - np.outer(xh, xh))
+        phis.append(up * (P_VEC @ xh))
+        E = hess @ P_VEC + omega ** 2 * u * P_VEC
+        if with_m:
+            E = E + 1j * omega * up * np.cross(xh, Q_VEC)
+            H = hess @ Q_VEC + omega ** 2 * u * Q_VEC - 1j * omega * up * np.cross(xh, P_VEC)
+        else:
+            H = -1j * omega * up * np.cross(xh, P_VEC)
+        Es.append(E)
+        Hs.append(H)
+    return np.array(phis), np.array(Es), np.array(Hs)
+
+
+def gaussian_density(grid, vec):
+    Z, Y, X = grid.coords()
+    g = g_of(np.sqrt(X * X + Y * Y + Z * Z))
+    return np.stack([vec[a] * g for a in range(3)]).astype(np.complex128)
+
+
+@pytest.mark.parametrize("omega", [0.0, 4 * math.pi])
+def test_scattered_potential_of_gaussian_current(omega):
+    grid = discrete.Grid(N)
+    kt = discrete.KernelTransforms(grid, omega)
+    J = gaussian_density(grid, P_VEC)
+    phi = operators.scattered_potential(kt, J)
+    idx, x = sample_points(grid)
+    ref, _, _ = reference_fields(x, omega, False)
+    got = phi[idx[:, 0], idx[:, 1], idx[:, 2]]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("with_m", [False, True])
+def test_maxwell_scattered_fields_of_gaussian_currents(with_m):
+    omega = 4 * math.pi
+    grid = discrete.Grid(N)
+    kt = discrete.KernelTransforms(grid, omega)
+    J = gaussian_density(grid, P_VEC)
+    JM = np.concatenate([J, gaussian_density(grid, Q_VEC)]) if with_m else J
+    EH = operators.scattered_em(kt, JM, reduced=not with_m)
+    idx, x = sample_points(grid, seed=1)
+    _, E, H = reference_fields(x, omega, with_m)
+    got_E = np.stack([EH[a][idx[:, 0], idx[:, 1], idx[:, 2]] for a in range(3)], -1)
+    got_H = np.stack([EH[3 + a][idx[:, 0], idx[:, 1], idx[:, 2]] for a in range(3)], -1)
+    scale = max(np.max(np.abs(E)), np.max(np.abs(H)))
+    assert np.max(np.abs(got_E - E)) <= 1e-12 * scale
+    assert np.max(np.abs(got_H - H)) <= 1e-12 * scale
+
+
+def test_planted_curl_sign_error_is_caught(monkeypatch):
+    """The same comparison with the sign of curl V flipped inside the oracle fails by O(1)."""
+    omega = 4 * math.pi
+    grid = discrete.Grid(N)
+    kt = discrete.KernelTransforms(grid, omega)
+    orig = operators.curl_V
+    monkeypatch.setattr(operators, "curl_V", lambda k, x: -orig(k, x))
+    EH = operators.scattered_em(kt, gaussian_density(grid, P_VEC), reduced=True)
+    idx, x = sample_points(grid, seed=1)
+    _, _, H = reference_fields(x, omega, False)
+    got_H = np.stack([EH[3 + a][idx[:, 0], idx[:, 1], idx[:, 2]] for a in range(3)], -1)
+    assert np.max(np.abs(got_H - H)) > 0.5 * np.max(np.abs(H))
