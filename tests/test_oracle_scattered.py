@@ -24,6 +24,9 @@ so the fields of the representations follow without any 3D machinery:
                       H = (Hess u) q + w^2 u q - i w u' (x^ x p).
 
 A dropped term, a flipped sign of the i w curl terms or a swapped J / M fails these.
+
+With the representation pinned, the Maxwell right-hand side and operator are pinned
+by the constitutive relations that their solution must satisfy (last tests).
 """
 import math
 
@@ -136,3 +139,46 @@ def test_planted_curl_sign_error_is_caught(monkeypatch):
     _, _, H = reference_fields(x, omega, False)
     got_H = np.stack([EH[3 + a][idx[:, 0], idx[:, 1], idx[:, 2]] for a in range(3)], -1)
     assert np.max(np.abs(got_H - H)) > 0.5 * np.max(np.abs(H))
+
+
+def _constitutive_residuals(with_mu):
+    import vie_inputs as vi
+    from oracle import solvers
+
+    n = 10
+    pm = vi.maxwell_problem(n=n, wavelengths=1.5, with_mu=with_mu, seed=3)
+    op = operators.OracleProblem.from_problem(pm)
+    d, p = pm.directions[0], pm.polarisations[0]
+    x, info = solvers.gmres(op.apply, op.rhs(d, p), tol=1e-14, restart=80)
+    assert info["converged"]
+    EH = op.scattered(x)
+    Z, Y, X = op.grid.coords()
+    ph = np.exp(1j * pm.omega * (d[0] * X + d[1] * Y + d[2] * Z))
+    dxp = np.cross(d, p)
+    E_tot = np.stack([p[a] * ph for a in range(3)]) + EH[:3]
+    H_tot = np.stack([dxp[a] * ph for a in range(3)]) + EH[3:]
+    eye = vi.identity_field(n)
+    J = x[:3]
+    res = [np.linalg.norm(J - np.einsum("ab...,b...->a...", pm.eps - eye, E_tot)) / np.linalg.norm(J)]
+    if with_mu:
+        M = x[3:]
+        res.append(np.linalg.norm(M - np.einsum("ab...,b...->a...", pm.mu - eye, H_tot)) / np.linalg.norm(M))
+    return res
+
+
+@pytest.mark.parametrize("with_mu", [False, True])
+def test_maxwell_solution_satisfies_the_constitutive_relations(with_mu):
+    """The scaled currents of Sec. 4 are J = (eps - I) E and M = (mu - I) H with the
+    total fields E = E_in + E_sc, H = H_in + H_sc.  The solution of Eq. (eq:intM) (or of
+    the reduced equation) with the oracle's right-hand side must satisfy both, with E_in
+    = p exp(i w d.x) and H_in = (d x p) exp(i w d.x) written out here and [E_sc; H_sc]
+    from the representation pinned above.  A wrong incident field in the right-hand side,
+    or an operator whose curl terms disagree with the representation, fails this."""
+    assert max(_constitutive_residuals(with_mu)) <= 1e-11
+
+
+def test_planted_incident_phase_error_is_caught(monkeypatch):
+    """The same relations with exp(-i w d.x) planted in the oracle's right-hand side fail by O(1)."""
+    orig = operators.rhs_maxwell
+    monkeypatch.setattr(operators, "rhs_maxwell", lambda g, He, Hm, w, d, p: orig(g, He, Hm, -w, d, p))
+    assert min(_constitutive_residuals(True)) > 0.5
