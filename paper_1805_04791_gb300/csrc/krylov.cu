@@ -97,6 +97,11 @@ vie_status run_rhs(vie_problem* P, const double* d, const double* p, int nrhs, v
 // layout of a group: vectors [r][L] (r < nb); Krylov basis [i][r][L].
 static const int kRedBlocks = 608;  // 4 x 152 SMs: the most blocks a reduction uses
 static const int kRedThreads = 256;
+// A sum of squares clamped at zero (rounding can leave it slightly negative),
+// with NaN kept: std::max(0.0, NaN) returns 0.0, which would turn a NaN
+// residual into a converged one and hide it from the non-finite checks.
+static inline double nonneg(double v) { return v < 0.0 ? 0.0 : v; }
+
 static const int kDotChunk = 8;
 // Blocks of a reduction over L elements: at least 8 elements per thread, so a
 // short vector does not pay for hundreds of idle blocks' reduction trees.
@@ -340,7 +345,7 @@ static vie_status norms_host(const double2* v, Group& g, std::vector<double>& ou
   VIE_CK(cudaMemcpyAsync(h.data(), g.hdev, sizeof(double2) * g.nb * g.HS, cudaMemcpyDeviceToHost, st));
   VIE_CK(cudaStreamSynchronize(st));
   out.resize(g.nb);
-  for (int r = 0; r < g.nb; ++r) out[r] = std::sqrt(std::max(0.0, h[(size_t)r * g.HS].x));
+  for (int r = 0; r < g.nb; ++r) out[r] = std::sqrt(nonneg(h[(size_t)r * g.HS].x));
   return VIE_OK;
 }
 
@@ -415,7 +420,7 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
       const double2* hr = &hb[(size_t)r * HS];
       const double w0 = hr[j + 1].x;
       double wn2 = reorth ? hr[H2 + j + 1].x : hr[j + 2].x;
-      const double hn = std::sqrt(std::max(0.0, wn2));
+      const double hn = std::sqrt(nonneg(wn2));
       if (!std::isfinite(hn) || !std::isfinite(w0)) {
         set_error("non-finite value in the Arnoldi process");
         return VIE_ENAN;
@@ -634,7 +639,7 @@ static vie_status run_bicgstab(vie_problem* P, const void* rhs, void* Jv, const 
     Dots4 q{{b, x, nullptr, nullptr}, {b, x, nullptr, nullptr}, 2};
     vie_status s = dots_host(q, L, partial, dev, d, st);
     if (s != VIE_OK) return s;
-    const double nb = std::sqrt(std::max(0.0, d[0].real())), nx = std::sqrt(std::max(0.0, d[1].real()));
+    const double nb = std::sqrt(nonneg(d[0].real())), nx = std::sqrt(nonneg(d[1].real()));
     if (!std::isfinite(nb)) {
       set_error("non-finite right-hand side");
       return VIE_ENAN;
@@ -661,7 +666,7 @@ static vie_status run_bicgstab(vie_problem* P, const void* rhs, void* Jv, const 
       q = Dots4{{rh, r, nullptr, nullptr}, {r, r, nullptr, nullptr}, 2};
       s = dots_host(q, L, partial, dev, d, st);
       if (s != VIE_OK) return s;
-      rel = std::sqrt(std::max(0.0, d[1].real())) / nb;
+      rel = std::sqrt(nonneg(d[1].real())) / nb;
       if (!std::isfinite(rel)) {
         set_error("non-finite residual");
         return VIE_ENAN;
@@ -686,9 +691,9 @@ static vie_status run_bicgstab(vie_problem* P, const void* rhs, void* Jv, const 
       q = Dots4{{sv, nullptr, nullptr, nullptr}, {sv, nullptr, nullptr, nullptr}, 1};
       s = dots_host(q, L, partial, dev, d, st);
       if (s != VIE_OK) return s;
-      if (std::sqrt(std::max(0.0, d[0].real())) / nb <= opt->tol) {
+      if (std::sqrt(nonneg(d[0].real())) / nb <= opt->tol) {
         k_lincomb<<<eb, 256, 0, st>>>(x, x, one, p, C(alpha), nullptr, zero, L);
-        rel = std::sqrt(std::max(0.0, d[0].real())) / nb;
+        rel = std::sqrt(nonneg(d[0].real())) / nb;
         conv = true;
         ++inf->inner_iters;
         break;
