@@ -1,18 +1,19 @@
 // Right-hand sides and the GMRES solve of (I + B + K) J = b.
 //
 // Sec. 1 and Sec. 6 name GMRES (and Bi-CGStab, used in Sec. 5) as the
-// iterative solvers for these second-kind equations.  Two modes:
+// iterative solvers for these second-kind equations.  Three modes:
 //  * FP64: restarted GMRES(m) on the FP64 apply, FP64 everywhere.
+//  * mixed: iterative refinement r = b - A x computed to FP64 accuracy (the
+//    double-word apply; VIE_RESIDUAL_FP64=1 takes the native FP64 apply),
+//    inner GMRES(m) on the FP32 apply with an FP32 Krylov basis; Hessenberg
+//    matrix, Givens rotations, least squares and the iterate x in FP64.
 //  * Bi-CGStab (the solver of Sec. 5) on the FP64 apply.
-//  * mixed: FP64 iterative refinement r = b - A x (FP64 apply), inner GMRES(m)
-//    on the FP32 apply with an FP32 Krylov basis; Hessenberg matrix, Givens
-//    rotations, least squares and the iterate x in FP64.
 // Arnoldi: classical Gram-Schmidt, one device reduction per step (inner
 // products and |w|^2 in one pass, the update and |w'|^2 in a second), and a
 // second Gram-Schmidt pass only when the first removed more than 3/4 of the
 // norm.  Reductions use a fixed order (reruns are bit-identical); per-thread
-// partial sums are FP64 for an FP64 basis and FP32 for an FP32 basis, the
-// cross-thread sums always FP64.
+// and warp sums are in the basis precision (FP64 or FP32), the cross-warp and
+// cross-block sums FP64.
 #include <cstdlib>
 #include <chrono>
 #include <cmath>
