@@ -2,8 +2,11 @@
 // and the scattered-field evaluation, as a pruned zero-padded 3D convolution
 // (Sec. 5: the truncated kernel transform applied with the FFT).
 //
-// Five passes over HBM, all shared-memory tiled with mixed-radix Stockham
-// FFTs (vie_fft.cuh):
+// Five passes over HBM.  For 2n in {64, 96, 128, 192, 256, 384, 512} they are the
+// register-resident kernels of apply_fast.cuh (chosen here, with the z-pass
+// autotuner); every other 2n = 2^a 3^b 5^c 7^d 11^e, and the double-word passes
+// without a fast kernel, run the shared-memory Stockham kernels of this file
+// (vie_fft.cuh):
 //   P1  x-lines: zero-pad n -> 2n, forward FFT          x [c][n][n][n]    -> A [c][n][n][2n]
 //   P2  y-lines: zero-pad, forward FFT                   A                 -> B [c][n][2n][2n]
 //   P3  z-pencils of all components: zero-pad, forward FFT, per-k kernel
@@ -24,7 +27,7 @@
 #include "apply_fast.cuh"
 
 namespace vie {
-// Generic kernels (any 2n = 2^a 3^b): shared-memory Stockham passes with the
+// Generic kernels (any 2n = 2^a 3^b 5^c 7^d 11^e): shared-memory Stockham passes with the
 // twiddle table staged in shared memory (vie_fft.cuh).
 // ---------------------------------------------------------------- P1
 template <typename T>

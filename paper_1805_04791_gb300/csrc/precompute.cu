@@ -1,4 +1,6 @@
-// Set-up kernels of a problem, all in FP64 on the device:
+// Set-up kernels of a problem, on the device, to FP64 accuracy (FP64 arithmetic,
+// except the kernel-transform cube FFTs, which run in double-word arithmetic on
+// the FP32 pipes unless VIE_SETUP_FP64=1):
 //  * H_eps = (eps + I)^-1 (eps - I) per node (Eq. (rhodef), Lemma 1), stored as
 //    the 6 entries of the symmetric tensor in FP64 and FP32;
 //  * the transform of the truncated Green's function (Sec. 5, steps a-b),
