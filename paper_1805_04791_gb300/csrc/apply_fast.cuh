@@ -70,7 +70,7 @@ __device__ __forceinline__ void slab_async(E* slab, const E* src, int narr, int 
 }
 
 // ------------------------------------------------ register-resident fast path
-// For 2n = R1 * R2 in {64, 128, 256, 512} every line is transformed by R2
+// For 2n = R1 * R2 in {64, 96, 128, 192, 256, 384, 512} every line is transformed by R2
 // threads with one shared-memory transpose per direction (vie_fft2.cuh).
 // Thread layouts: "row" passes (x-lines, contiguous) put the R2 threads of a
 // line on consecutive lanes; "column" passes (y- and z-lines, one line per
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256) f_py(const typename CT<T>::V* __restrict_
 // of its pencil (pruned forward FFT), parks the spectrum in shared memory,
 // then each output group forms its component of the kernel product from the
 // three (or six) input spectra and runs the pruned inverse FFT.  Keeping one
-// component per thread holds registers near 64, so 2 CTAs (24 warps) fit an
-// SM.  CTA order pairs mirror pencils (ky, M - ky) x (kx tile, mirrored tile)
+// component per thread holds registers near 80 (2n = 256: 2 CTAs, 24 warps,
+// per SM).  CTA order pairs mirror pencils (ky, M - ky) x (kx tile, mirrored tile)
 // so the four CTAs reading the same kernel octant entries share them in L2.
 template <int MODE> struct ModeDim;
 template <> struct ModeDim<KM_SYM3> { static constexpr int CI = 3, CO = 3, NT = 3; };
