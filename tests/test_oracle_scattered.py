@@ -182,3 +182,49 @@ def test_planted_incident_phase_error_is_caught(monkeypatch):
     orig = operators.rhs_maxwell
     monkeypatch.setattr(operators, "rhs_maxwell", lambda g, He, Hm, w, d, p: orig(g, He, Hm, -w, d, p))
     assert min(_constitutive_residuals(True)) > 0.5
+
+
+def _scalar_constitutive_residual(kind, plant_printed_sign=False):
+    """|| J - X (grad phi_in + grad div V J) || / || J || for the Laplace (X = eps - I) or
+    Helmholtz (X = eps^-1 - I) solution, with grad phi_in written out here."""
+    import vie_inputs as vi
+    from oracle import solvers
+
+    n = 10
+    if kind == "laplace":
+        p = vi.laplace_bump_problem(n=n, seed=4)
+    else:
+        p = vi.helmholtz_problem(n=n, wavelengths=1.5, seed=4)
+    op = operators.OracleProblem.from_problem(p)
+    d = p.directions[0]
+    apply = op.apply
+    if plant_printed_sign:  # the "+2 H_{eps^-1}" of the printed Eq. (eq:intH)
+        apply = lambda x: x + 2.0 * operators.tmul(op.Hinv, operators.T_op(op.kt, x))
+    J, info = solvers.gmres(apply, op.rhs(d), tol=1e-14, restart=80)
+    assert info["converged"]
+    Z, Y, X = op.grid.coords()
+    if kind == "laplace":
+        grad_in = np.stack([np.full(Z.shape, -d[a], np.complex128) + 0 * X * Y for a in range(3)])
+        Xt = p.eps - vi.identity_field(n)
+    else:
+        ph = np.exp(1j * p.omega * (d[0] * X + d[1] * Y + d[2] * Z))
+        grad_in = np.stack([1j * p.omega * d[a] * ph for a in range(3)])
+        Xt = operators.inverse_field(p.eps) - vi.identity_field(n)
+    grad_tot = grad_in + operators.grad_div_V(op.kt, J)  # grad phi_sc = grad div V J
+    return np.linalg.norm(J - np.einsum("ab...,b...->a...", Xt, grad_tot)) / np.linalg.norm(J)
+
+
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_scalar_solutions_satisfy_their_defining_relation(kind):
+    """Sec. 2 and the existence proof of Sec. 3 start from J = X (grad phi_in + grad
+    div V J) with X = eps - I (Laplace) or eps^-1 - I (Helmholtz) and turn it into
+    Eqs. (eq:intLap) / (eq:intH) by adding J/2 and multiplying by 2 (X + 2I)^-1; the
+    oracle's solution must satisfy the starting relation, with grad phi_in = -E0 or
+    i w d exp(i w d.x) written out here."""
+    assert _scalar_constitutive_residual(kind) <= 1e-11
+
+
+def test_printed_helmholtz_sign_fails_the_defining_relation():
+    """With the printed "+2 H" the solution no longer satisfies the relation the
+    derivation starts from (the reading that keeps the derived minus sign)."""
+    assert _scalar_constitutive_residual("helmholtz", plant_printed_sign=True) > 1e-2
