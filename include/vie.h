@@ -174,9 +174,11 @@ vie_status vie_apply_static(vie_problem* P, const void* x, void* y, int precisio
 /* Right-hand sides for plane-wave (or uniform-field) incidence, FP64 complex,
  * [nrhs][c][n][n][n] into device buffer rhs_out.
  *   d  host, [nrhs][3]: Laplace: the applied field E0 (grad phi_in = -E0);
- *      Helmholtz / Maxwell: unit propagation direction, phi_in = exp(i w d.x).
+ *      Helmholtz / Maxwell: unit propagation direction, phi_in = exp(i w d.x)
+ *      (| |d| - 1 | > 1e-8 returns VIE_EINVAL).
  *   p  host, [nrhs][3]: Maxwell polarisation (E_in = p exp(i w d.x),
- *      H_in = d x p exp(i w d.x)); ignored otherwise (may be NULL).
+ *      H_in = d x p exp(i w d.x)), perpendicular to d (|d.p| > 1e-8 |p| returns
+ *      VIE_EINVAL); ignored otherwise (may be NULL).
  * Laplace: 2 H_eps grad phi_in (Eq. (eq:intLap)); Helmholtz: 2 H_{eps^-1} grad phi_in
  * (Eq. (eq:intH)); Maxwell: [2 H_eps E_in; 2 H_mu H_in] (Eq. (eq:intM)). */
 vie_status vie_rhs_plane_wave(vie_problem* P, const double* d, const double* p, int nrhs, void* rhs_out,

@@ -164,6 +164,26 @@ vie_status vie_rhs_plane_wave(vie_problem* P, const double* d, const double* p, 
     set_error("vie_rhs_plane_wave: bad argument");
     return VIE_EINVAL;
   }
+  // a plane wave needs a unit propagation direction (|d| fixes the wavenumber w |d|)
+  // and, for Maxwell, a transverse polarisation (d . p = 0, else E_in is not a
+  // solution of the free-space equations); Laplace's d is the field E0 itself
+  for (int r = 0; r < nrhs && P->kind != VIE_LAPLACE; ++r) {
+    const double* dr = d + 3 * (size_t)r;
+    const double dn = std::sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+    if (!(std::fabs(dn - 1.0) <= 1e-8)) {
+      set_error("vie_rhs_plane_wave: d must be a unit vector");
+      return VIE_EINVAL;
+    }
+    if (P->kind == VIE_MAXWELL) {
+      const double* pr = p + 3 * (size_t)r;
+      const double pn = std::sqrt(pr[0] * pr[0] + pr[1] * pr[1] + pr[2] * pr[2]);
+      const double dp = dr[0] * pr[0] + dr[1] * pr[1] + dr[2] * pr[2];
+      if (!std::isfinite(pn) || !(std::fabs(dp) <= 1e-8 * pn)) {
+        set_error("vie_rhs_plane_wave: p must be finite and perpendicular to d");
+        return VIE_EINVAL;
+      }
+    }
+  }
   return run_rhs(P, d, p, nrhs, rhs_out, (cudaStream_t)stream);
 }
 

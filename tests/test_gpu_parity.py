@@ -283,6 +283,19 @@ def test_invalid_arguments(vie):
         vie.vie_apply(P.handle, x, x, vie.VIE_FP64)
     with pytest.raises(vie.VieError):
         vie.vie_apply(P.handle, x, torch.empty_like(x), 7)
+    # plane waves: unit directions, transverse polarisations (Laplace's d is E0: any vector)
+    b3 = torch.empty((3, 8, 8, 8), dtype=torch.complex128, device="cuda:0")
+    P.rhs(np.array([0.0, 0.0, 2.5]), None, 1, b3)
+    for kind in ("helmholtz", "maxwell"):
+        Q = vie.Problem(kind, 8, -1.0, 1.0, 2.0, e)
+        pol = np.array([1.0, 0.0, 0.0]) if kind == "maxwell" else None
+        Q.rhs(np.array([0.0, 0.6, 0.8]), pol, 1, b3)
+        for dd, pp in ((np.array([0.0, 0.0, 2.0]), pol), (np.array([0.0, 0.0, np.nan]), pol)) + \
+                (((np.array([0.0, 0.6, 0.8]), np.array([0.0, 1.0, 0.0])),) if kind == "maxwell" else ()):
+            with pytest.raises(vie.VieError) as ei:
+                Q.rhs(dd, pp, 1, b3)
+            assert ei.value.status == vie.VIE_EINVAL
+        Q.close()
     # a valid apply first: buffers that touch without sharing a byte are accepted
     N = 8 ** 3
     f32 = torch.zeros(2 * 3 * N, dtype=torch.complex64, device="cuda:0")
