@@ -104,6 +104,10 @@ typedef struct {
                         steps need only reach the overall target) */
   int mode;          /* vie_solve_mode */
   int nrhs;          /* number of right-hand sides, solved independently (>= 1) */
+  int check_fp64;    /* 1: after the solve, compute the residual of the final
+                        iterate once more with the native FP64 apply (one extra
+                        FP64 apply per right-hand side) into
+                        info->rel_residual_fp64; 0: skip it (reported as -1) */
 } vie_solve_opts;
 
 typedef struct {
@@ -112,8 +116,14 @@ typedef struct {
   int applies_fp32;
   int applies_fp64;       /* FP64-accuracy applies: native FP64, or VIE_DF64 for the mixed
                              mode's refinement residuals (VIE_RESIDUAL_FP64=1: native) */
-  double rel_residual;    /* max over right-hand sides of the final FP64 relative residual */
+  double rel_residual;    /* max over right-hand sides of the final relative residual, as the
+                             solver computed it: native FP64 (FP64, Bi-CGStab) or double-word
+                             (mixed; relative error of that apply near 1e-13) */
   double t_solve;         /* wall seconds spent in vie_solve */
+  double t_precompute;    /* wall seconds vie_problem_create spent on this handle's set-up
+                             (medium tensors and kernel transforms, Sec. 5) */
+  double rel_residual_fp64; /* max over right-hand sides of ||b - A J|| / ||b|| of the returned
+                               J with the native FP64 apply (opts->check_fp64 = 1), else -1 */
 } vie_solve_info;
 
 /* Create a problem: grid, medium and frequency (Sec. 2 / Eq. (Laplace_Scalar),
@@ -148,27 +158,32 @@ int vie_problem_ncomp(const vie_problem* P);
  *   of the FP64 kernel and medium tables, kept until destroy). */
 vie_status vie_apply(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
 
-/* y = (I + B + K) x like vie_apply, for callers that cannot allocate device
- * memory when they apply the operator: code being recorded into a CUDA graph by
- * stream capture, solvers inside frameworks that own all device memory through
- * their own arena, and latency-bound loops that must not take the device-wide
- * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this
- * is an interface addition.
+/* y = (I + B + K) x like vie_apply, for callers that cannot let the library
+ * allocate device memory when they apply the operator: solvers embedded in
+ * frameworks that own all device memory through their own arena or pool (an
+ * allocation outside it fails or takes memory promised elsewhere), and
+ * latency-bound loops that must not take the device-wide synchronisation of
+ * cudaMalloc/cudaFree or risk running out of memory in the middle of a run.
+ * The paper has no counterpart; this is an interface addition.
  *   Scratch: the padded intermediates live in one file-scope device array of
  *   64 MiB per device (held by every GPU that loads the library until the
  *   process exits).  Sizes whose workspace exceeds it return VIE_EINVAL; with 3
  *   components and nrhs = 1 that allows n <= 77 in FP32 and n <= 61 in FP64.
  *   The call allocates nothing: no cudaMalloc/cudaFree or allocating library
  *   routine.  Its first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
- *   The z-pass schedule must already be chosen for this precision (vie_tune,
- *   or one vie_apply), otherwise VIE_EINVAL.
+ *   (cudaGetSymbolAddress) while that device is current; make that first call
+ *   before any stream capture.
+ *   The z-pass schedule must already be chosen for this precision and grid
+ *   size -- by vie_tune or one vie_apply on this handle, or on any handle of
+ *   the process with the same grid size and kind (the choice is shared
+ *   process-wide) -- otherwise VIE_EINVAL: choosing it would launch and time
+ *   candidates.  Sizes that run the generic kernels need no choice.
  *   Every call shares the array and leaves its contents behind (no pass reads
  *   scratch it did not write first); calls that overlap on the GPU -- on
  *   different streams or different handles -- race on it and must be ordered
  *   by the caller.
  *   x, y, nrhs, stream: as for vie_apply; precision VIE_FP64 or VIE_FP32
- *   (VIE_DF64 returns VIE_EINVAL). */
+ *   (VIE_DF64 returns VIE_EINVAL).  The result equals vie_apply's bit for bit. */
 vie_status vie_apply_static(vie_problem* P, const void* x, void* y, int precision, int nrhs, void* stream);
 
 /* Right-hand sides for plane-wave (or uniform-field) incidence, FP64 complex,

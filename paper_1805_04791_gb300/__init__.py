@@ -43,12 +43,13 @@ class VieError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("mode", ctypes.c_int),
-                ("nrhs", ctypes.c_int)]
+                ("nrhs", ctypes.c_int), ("check_fp64", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("applies_fp32", ctypes.c_int),
-                ("applies_fp64", ctypes.c_int), ("rel_residual", ctypes.c_double), ("t_solve", ctypes.c_double)]
+                ("applies_fp64", ctypes.c_int), ("rel_residual", ctypes.c_double), ("t_solve", ctypes.c_double),
+                ("t_precompute", ctypes.c_double), ("rel_residual_fp64", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -263,8 +264,8 @@ class Problem:
         vie_rhs_plane_wave(self.handle, d, p, nrhs, out, stream)
 
     def solve(self, rhs, J, tol=1e-10, restart=50, max_outer=50, max_inner=2000, inner_tol=1e-5,
-              mode=VIE_SOLVE_FP64, nrhs=1, stream=None, allow_noconv=False):
-        opts = SolveOpts(tol, restart, max_outer, max_inner, inner_tol, mode, nrhs)
+              mode=VIE_SOLVE_FP64, nrhs=1, stream=None, allow_noconv=False, check_fp64=False):
+        opts = SolveOpts(tol, restart, max_outer, max_inner, inner_tol, mode, nrhs, 1 if check_fp64 else 0)
         return vie_solve(self.handle, rhs, J, opts, stream, allow_noconv)
 
     def eval_scattered(self, J, out, nrhs=1, stream=None):

@@ -301,6 +301,21 @@ static std::map<long long, int>& tune_cache() {
   static std::map<long long, int> c;
   return c;
 }
+// Key of the process-wide z-pass choice: one per (n, precision, kernel mode).
+static long long tune_key(const vie_problem* P, int prec, int mode) { return ((long long)P->n * 4 + prec) * 8 + mode; }
+
+bool p3_schedule_ready(vie_problem* P, const KernelSet& K, int prec) {
+  if (prec == VIE_DF64) return true;                       // one fixed schedule
+  if (!fast_select(2 * P->n, K.mode, true).p3) return true;  // generic kernels
+  int& v = P->p3_variant[prec][K.mode];
+  if (v >= 0) return true;
+  if (getenv("VIE_P3_VARIANT")) return true;  // a forced variant is launched untimed
+  std::lock_guard<std::mutex> g(tune_mutex());
+  auto it = tune_cache().find(tune_key(P, prec, K.mode));
+  if (it == tune_cache().end()) return false;
+  v = it->second;
+  return true;
+}
 
 
 static vie_status fast_dispatch(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
@@ -383,7 +398,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     // one decision per (n, precision, mode) per process: every problem of a
     // shape then runs the same arithmetic (bitwise-reproducible results).  A
     // variant forced with VIE_P3_VARIANT bypasses the cache both ways.
-    const long long key = ((long long)P->n * 4 + Prec<T>::id) * 8 + K.mode;
+    const long long key = tune_key(P, Prec<T>::id, K.mode);
     const bool forced = getenv("VIE_P3_VARIANT") != nullptr;
     if (!forced) {
       std::lock_guard<std::mutex> g(tune_mutex());
@@ -492,7 +507,7 @@ vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant
   v = -1;
   {
     std::lock_guard<std::mutex> g(tune_mutex());
-    tune_cache().erase(((long long)P->n * 4 + prec) * 8 + K.mode);
+    tune_cache().erase(tune_key(P, prec, K.mode));
   }
   // an apply of a zero vector allocates the workspace and tunes on its first call
   const long long L = (long long)cin_of(K.mode) * P->n * P->n * P->n;

@@ -1,17 +1,17 @@
 // vie_apply_static: the operator apply with its scratch in a fixed device
 // array instead of memory the library allocates.
 //
-// Some callers cannot allocate device memory at the point where they apply
-// the operator: code recorded into a CUDA graph by stream capture (cudaMalloc
-// is not a stream operation and breaks or synchronises the capture), solvers
-// embedded in frameworks that own the whole device memory through their own
-// arena, and latency-bound loops that may not take the device-wide
-// synchronisation a cudaMalloc/cudaFree can cause.  For them the five passes
-// of the apply use the file-scope array below as their padded intermediates.
-// The array is a fixed kStaticScratchBytes per device and stays resident,
-// for every GPU that loads the library, until the process exits.
+// Some callers cannot let a library allocate device memory at the point where
+// they apply the operator: solvers embedded in frameworks that own the whole
+// device memory through their own arena or pool (a cudaMalloc there fails, or
+// takes memory the arena has promised elsewhere), and latency-bound loops that
+// may not take the device-wide synchronisation a cudaMalloc/cudaFree can cause
+// or the risk of an out-of-memory failure in the middle of a run.  For them
+// the five passes of the apply use the file-scope array below as their padded
+// intermediates.  The array is a fixed kStaticScratchBytes per device and
+// stays resident, for every GPU that loads the library, until the process
+// exits.
 #include <algorithm>
-#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -69,15 +69,12 @@ extern "C" vie_status vie_apply_static(vie_problem* P, const void* x, void* y, i
               std::to_string(kStaticScratchBytes));
     return VIE_EINVAL;
   }
-  // the z-pass schedule must already be chosen: tuning would create events
-  if (P->p3_variant[precision == VIE_FP64 ? 0 : 1][K.mode] < 0) {
-    const int M = 2 * P->n;
-    const bool fast = (M == 64 || M == 96 || M == 128 || M == 192 || M == 256 || M == 384 || M == 512) &&
-                      !getenv("VIE_GENERIC_FFT");
-    if (fast) {
-      set_error("vie_apply_static: call vie_tune (or vie_apply once) for this precision first");
-      return VIE_EINVAL;
-    }
+  // the z-pass schedule must already be chosen (by this handle, or for this
+  // shape by any handle of the process): choosing it would time candidates
+  // with events and launch them on the scratch
+  if (!p3_schedule_ready(P, K, precision)) {
+    set_error("vie_apply_static: call vie_tune (or vie_apply once) for this precision and grid size first");
+    return VIE_EINVAL;
   }
   void* scratch = nullptr;
   vie_status s = scratch_address(&scratch);

@@ -1,5 +1,6 @@
 // extern "C" entry points of include/vie.h: argument checks, handle life
 // cycle and dispatch to the set-up, apply and solver translation units.
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -107,6 +108,7 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
     return VIE_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const auto t_start = std::chrono::steady_clock::now();
   vie_problem* P = new vie_problem();
   P->kind = kind;
   P->n = n;
@@ -139,6 +141,7 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
     free_problem(P);
     return s;
   }
+  P->t_precompute = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   *out = P;
   return VIE_OK;
 }
@@ -192,7 +195,8 @@ vie_status vie_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_o
   if (!P || !rhs || !J || !opt || opt->nrhs < 1 || opt->restart < 1 || opt->restart > 200 || !(opt->tol > 0) ||
       opt->max_inner < 1 || opt->max_outer < 0 ||
       (opt->mode == VIE_SOLVE_MIXED && !(opt->inner_tol > 0 && opt->inner_tol < 1)) ||
-      (opt->mode != VIE_SOLVE_FP64 && opt->mode != VIE_SOLVE_MIXED && opt->mode != VIE_SOLVE_BICGSTAB)) {
+      (opt->mode != VIE_SOLVE_FP64 && opt->mode != VIE_SOLVE_MIXED && opt->mode != VIE_SOLVE_BICGSTAB) ||
+      (opt->check_fp64 != 0 && opt->check_fp64 != 1)) {
     set_error("vie_solve: bad argument");
     return VIE_EINVAL;
   }

@@ -90,6 +90,7 @@ struct vie_problem {
   vie::Profiler prof;
   int p3_variant[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // tuned z-pass variant per (precision, mode)
   int* dflag = nullptr;      // device error flag (NaN, bad input)
+  double t_precompute = 0;   // wall seconds of the set-up in vie_problem_create
 };
 
 namespace vie {
@@ -128,6 +129,12 @@ vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* o
 size_t apply_workspace_bytes(int n, int c, int nrhs, int prec);
 // Pick (by timing, unless VIE_TUNE=0) the z-pass variant for (prec, K.mode); returns it in *variant.
 vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant, cudaStream_t st);
+// Whether run_apply at this precision can start without choosing a z-pass
+// schedule (no tuning launches, no timing events): the shape runs the generic
+// kernels or one fixed schedule, the handle holds its choice, a variant is
+// forced (VIE_P3_VARIANT), or the process-wide cache has this shape's choice,
+// which is then copied into the handle.
+bool p3_schedule_ready(vie_problem* P, const KernelSet& K, int prec);
 
 // krylov.cu
 vie_status run_solve(vie_problem* P, const void* rhs, void* J, const vie_solve_opts* opt, vie_solve_info* info,

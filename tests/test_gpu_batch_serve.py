@@ -51,21 +51,39 @@ def test_batched_equals_single_fp64(vie, monkeypatch):
     P.close()
 
 
+def _serving_oracle_solution(req):
+    """The oracle's FP64 GMRES solution of one served request: the same medium
+    formula (the anisotropic bump with the request's seed, evaluated on the
+    host), frequency, incident wave and discrete operator."""
+    rng = vi.SplitMix64(req.seed)
+    eps = vi.anisotropic_bump(req.n, -1.0, 1.0, 0.5, 0.1, rng).real.astype(np.complex128)
+    omega = 2.0 * np.pi * req.wavelengths / 2.0
+    op = operators.OracleProblem(req.kind, req.n, -1.0, 1.0, omega, eps, None)
+    pol = req.polarisation if req.kind == "maxwell" else None
+    Jo, info = solvers.gmres(op.apply, op.rhs(req.direction, pol), tol=1e-12, restart=60, maxiter=800)
+    assert info["converged"]
+    return Jo
+
+
 def test_serving_mix_completes_and_is_mix_invariant(vie):
     """Requests of different sizes and kinds overlap on the device; a request's
-    result is the same alone and inside the mix."""
+    result is the same alone and inside the mix, and every served solution
+    equals the oracle's solution of that request."""
     from paper_1805_04791_gb300 import serve
 
     reqs = vi.serving_mix(10, rate_per_s=200.0, seed=4, sizes=(16, 24, 32), wl_range=(1.0, 3.0))
     target = reqs[3]
-    alone = serve.Server(budget_bytes=8e9, max_slots=1, keep_solutions=True).run([target])
+    alone = serve.Server(budget_bytes=8e9, max_slots=1, keep_solutions=True, tol=1e-10).run([target])
     assert alone.results[0].status == "ok", alone.results[0].status
-    mix = serve.Server(budget_bytes=8e9, max_slots=6, keep_solutions=True).run(reqs)
+    mix = serve.Server(budget_bytes=8e9, max_slots=6, keep_solutions=True, tol=1e-10).run(reqs)
     s = mix.summary()
     assert s["completed"] == 10, [r.status for r in mix.results]
     assert s["peak_inflight"] >= 2  # requests really overlapped
+    by_id = {r.rid: r for r in reqs}
     for r in mix.results:
-        assert r.rel_residual <= 1e-8
+        assert r.rel_residual <= 1e-10
+        # mixed solve to 1e-10 on a second-kind operator: solution error ~1e-9
+        assert rel(r.solution, _serving_oracle_solution(by_id[r.rid])) <= 1e-8, (r.rid, r.kind, r.n)
     got = [r for r in mix.results if r.rid == target.rid][0]
     a, m = alone.results[0].solution, got.solution
     assert rel(m, a) <= 1e-12
