@@ -236,7 +236,11 @@ vie_status vie_problem_destroy(vie_problem* P);
  * thread packed as f32x2 lanes; 7/8/9 (FP32 only, same sizes) mirror-group
  * CTAs of 8/4/16 pencils with all three components of a vector per thread;
  * 10/11 as 7/8 with a grid sized to the device, each CTA walking several
- * mirror groups and prefetching the next one's inputs and kernel values.
+ * mirror groups and prefetching the next one's inputs and kernel values;
+ * 12/13/14 (FP32, 3x3 symmetric and divergence kernel sets, same sizes) slim
+ * component-group CTAs of 8/8/4 pencils sized for 3/2/5 CTAs per SM: one
+ * transpose line per pencil shared by the components in turn, 16-byte
+ * shared-memory reads, packed f32x2 kernel mixing.
  * Every candidate runs once untimed, then two rounds of three timed launches;
  * each keeps its best round and the fastest is chosen.  VIE_DF64 has one fixed
  * schedule (*variant = -1).  vie_apply

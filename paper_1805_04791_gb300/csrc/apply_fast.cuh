@@ -766,6 +766,258 @@ f_p3t(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
   }
 }
 
+// z-pencils, slim component-group variant (FP32; 3x3 symmetric and
+// divergence mixing).  Same mirror-group CTA and register layout as f_p3t (each
+// thread carries the three components of a vector on its pencil), re-balanced
+// for occupancy and for fewer shared-memory instructions:
+//  * one transpose line per pencil instead of three: the components go
+//    through it one after the other (two barriers per component and
+//    direction), so a CTA of NP = 8 pencils at 2n = 256 needs ~75 KB of shared
+//    memory and three CTAs share an SM (registers capped for MINB CTAs);
+//  * transpose rows have an even pitch, so each thread reads its row back as
+//    16-byte pairs (the writes stay 8-byte, column-wise);
+//  * the kernel slab is stored [q][z][array]: the 6 (or 3) octant values of a
+//    point are adjacent and arrive in three (two) 16-byte loads;
+//  * twiddles come from a per-thread table W^{t k1} read as 16-byte pairs;
+//  * only the next component's inputs are loaded ahead (16 registers instead
+//    of the 48 of a whole next tile);
+//  * the kernel mixing runs on packed f32x2 arithmetic with broadcast operands:
+//    y += K x as y + K.x (x.x, x.y) + K.y (-x.y, x.x), two packed instructions
+//    per complex multiply-add instead of four scalar ones;
+//  * the sign of each octant value is fixed per tile in kx and ky and, taking
+//    "k >= n" as the mirrored half (odd arrays vanish at k = n), at compile time
+//    in kz.
+template <int R1, int R2, int MODE, int NP>
+struct P3sCfg {
+  static constexpr int NARR = (MODE == KM_SYM3) ? 6 : 3;
+  static constexpr int NARRP = (NARR + 1) & ~1;  // values per slab point, padded to 16 bytes
+  static constexpr int M = R1 * R2;
+  static constexpr int PF = R2 + 2, PI = R1 + 2;  // even row pitches: 16-byte row reads
+  static constexpr int LS0 = R1 * PF > R2 * PI ? R1 * PF : R2 * PI;
+  static constexpr int LS = ((LS0 + 13) / 16) * 16 + 2;  // = 2 mod 16: conflict-free column writes
+  static constexpr int QW = NP + 1;
+  static constexpr int O = M / 2 + 1;  // octant extent (odd: conflict-free 16-byte slab reads)
+  static constexpr int NTHR = NP * R2;
+  // W^{t k1} [t][k1] with rows of R1 + 2, and [k1][n2] with rows of R2 + 2 when R1 != R2 (the
+  // padding spreads the 16-byte pair reads of different rows over the banks)
+  static constexpr int TP1 = R1 + 2, TP2 = R2 + 2;
+  static constexpr int NTW = (R1 == R2) ? R2 * TP1 : R2 * TP1 + R1 * TP2;
+  static constexpr long long SMEM = 8LL * (NTW + (long long)NP * LS + (long long)QW * O * NARRP);
+};
+
+__device__ __forceinline__ float2 bcx2(float2 a) { return make_float2(a.x, a.x); }
+__device__ __forceinline__ float2 bcy2(float2 a) { return make_float2(a.y, a.y); }
+// i a
+__device__ __forceinline__ float2 ipx(float2 a) { return make_float2(-a.y, a.x); }
+
+template <int R1, int R2, int MODE, int NP, int MINB>
+__global__ void __launch_bounds__(NP * R2, MINB)
+f_p3s(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const float2* __restrict__ twg) {
+  typedef float T;
+  typedef float2 V;
+  typedef Fft2<T, R1, R2> F;
+  typedef P3sCfg<R1, R2, MODE, NP> Cfg;
+  constexpr int G = 3;                          // components per thread
+  constexpr int GO = (MODE == KM_DIV) ? 1 : 3;  // output components per thread
+  constexpr int NARR = Cfg::NARR, NARRP = Cfg::NARRP;
+  constexpr int M = F::M, NTX = M / NP, NTHR = NP * R2, H = R1 / 2;
+  constexpr int NGROUPS = (M / 2 + 1) * (NTX / 2);
+  constexpr int LS = Cfg::LS, QW = Cfg::QW, PF = Cfg::PF, PI = Cfg::PI;
+  // the grid size is fixed by the transform length (n = M / 2): strides and
+  // the octant extent are compile-time constants
+  constexpr int NN = M / 2, O = Cfg::O;
+  constexpr long long O3 = (long long)O * O * O;
+  constexpr long long zs = (long long)M * M, cs = (long long)NN * zs;
+  static_assert(MODE == KM_SYM3 || MODE == KM_DIV, "slim z pass: 3x3 symmetric or divergence mixing");
+  static_assert(R1 % 2 == 0 && R2 % 2 == 0 && (R1 % R2 == 0 || R1 < 2 * R2), "thread layout of Fft2");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int TP1 = Cfg::TP1, TP2 = Cfg::TP2;
+  V* tw1 = (V*)smraw;                             // [t < R2][k1 < R1] = W^{t k1}, row pitch TP1
+  V* tw2 = (R1 == R2) ? tw1 : tw1 + R2 * TP1;     // [k1 < R1][n2 < R2] = W^{k1 n2}, row pitch TP2
+  V* sm = tw1 + Cfg::NTW;
+  V* slab = sm + NP * LS;                     // [q < QW][oz < O][a < NARRP]
+  // consecutive lanes hold consecutive pencils (coalesced 64-byte rows of B);
+  // a pencil's R2 threads lie in different warps, so its transposes take the
+  // CTA barrier (a layout with each pencil's threads in one warp, which needs
+  // only warp synchronisation, measured 1.65x slower: 8-byte accesses to 16
+  // different z planes per warp instruction)
+  const int l = threadIdx.x % NP, t = threadIdx.x / NP;
+  auto line_sync = [] { __syncthreads(); };
+  const int b0 = blockIdx.y;
+  const int grp = blockIdx.x;
+  if (grp >= NGROUPS) return;  // block-uniform
+  const int kyp = grp / (NTX / 2), txp = grp - (grp / (NTX / 2)) * (NTX / 2);
+  const bool self_y = (kyp == 0 || kyp == M / 2);
+  {  // kernel slab <- K[a][oz][kyp][NP txp + q], in flight while tile 0 starts
+    const V* src = K + (long long)kyp * O + NP * txp;
+    for (int a = 0; a < NARR; ++a)
+      for (int idx = threadIdx.x; idx < O * QW; idx += NTHR) {
+        const int oz = idx / QW, q = idx - oz * QW;
+        cp_async<8>(slab + (q * O + oz) * NARRP + a, src + a * O3 + (long long)oz * O * O + q);
+      }
+    cp_async_commit();
+  }
+  for (int j = threadIdx.x; j < R2 * R1; j += NTHR) {
+    const int r = j / R1, c = j - r * R1;
+    tw1[r * TP1 + c] = twg[r * c];
+  }
+  if (R1 != R2)
+    for (int j = threadIdx.x; j < R1 * R2; j += NTHR) {
+      const int r = j / R2, c = j - r * R2;
+      tw2[r * TP2 + c] = twg[r * c];
+    }
+  V* s = sm + l * LS;  // this pencil's transpose line
+  // inputs (z < n) of one component: the next one is loaded while the current one is transformed
+  V g[H];
+  auto load_comp = [&](const V* base, int c) {
+#pragma unroll
+    for (int n1 = 0; n1 < H; ++n1) g[n1] = base[c * cs + (long long)(R2 * n1 + t) * zs];
+  };
+  auto tile_base = [&](int v) {
+    const int ky = (v & 1) ? M - kyp : kyp;
+    const int tile = (v & 2) ? NTX - 1 - txp : txp;
+    return B + (long long)b0 * C * cs + (long long)ky * M + tile * NP + l;
+  };
+  load_comp(tile_base(0), 0);
+  __syncthreads();  // twiddle tables visible
+  const float4* twf = (const float4*)(tw1 + t * TP1);  // W^{t k1}, k1 pairs
+#pragma unroll 1
+  for (int v = 0; v < 4; ++v) {
+    if ((v & 1) && self_y) continue;  // block-uniform
+    const int ky = (v & 1) ? M - kyp : kyp;
+    const int tile = (v & 2) ? NTX - 1 - txp : txp;
+    const int kx = tile * NP + l;
+    V* colbase = B + (long long)b0 * C * cs + (long long)ky * M + kx;
+    V X[G][F::J][R2];
+    // ---- forward z transforms, one component at a time through the line
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+      V u[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) u[n1] = (n1 < H) ? g[n1] : make_float2(0.f, 0.f);
+      if (c + 1 < G) load_comp(colbase, c + 1);
+      dft_half_in<R1, -1, T>(u);
+#pragma unroll
+      for (int k2 = 0; k2 < R1 / 2; ++k2) {
+        const float4 w = twf[k2];
+        if (k2 > 0) u[2 * k2] = cmul(u[2 * k2], make_float2(w.x, w.y));
+        u[2 * k2 + 1] = cmul(u[2 * k2 + 1], make_float2(w.z, w.w));
+      }
+      line_sync();  // earlier readers of the line are done
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) s[k1 * PF + t] = u[k1];
+      line_sync();
+#pragma unroll
+      for (int j = 0; j < F::J; ++j) {
+        if (!F::row(t, j)) continue;
+        const int k1 = t + R2 * j;
+        const float4* row = (const float4*)(s + k1 * PF);
+#pragma unroll
+        for (int n2 = 0; n2 < R2 / 2; ++n2) {
+          const float4 r = row[n2];
+          X[c][j][2 * n2] = make_float2(r.x, r.y);
+          X[c][j][2 * n2 + 1] = make_float2(r.z, r.w);
+        }
+        Dft<R2, -1, T>::run(X[c][j]);
+      }
+    }
+    if (v == 0) {           // block-uniform
+      cp_async_wait_all();  // the kernel slab
+      __syncthreads();      // slab visible to every thread
+    }
+    line_sync();  // the line is free again
+    // ---- the next tile's first component, loaded during the mixing and the inverse
+    const int vn = self_y ? (v == 0 ? 2 : 4) : v + 1;  // self-mirrored rows run tiles 0 and 2 only
+    if (vn < 4) load_comp(tile_base(vn), 0);
+    // ---- kernel mixing on registers
+    {
+      const bool fy = ky >= NN, fx = kx >= NN;  // tile-uniform
+      const V* kq = slab + ((fx ? M - kx : kx) - NP * txp) * O * NARRP;
+      float sg0[NARR], sg1[NARR];  // sign of array a for kz < n and kz >= n
+#pragma unroll
+      for (int a = 0; a < NARR; ++a) {
+        const int par = sym_parity(MODE == KM_DIV ? 6 + a : a);
+        const bool ng = ((par & 2) && fy) != ((par & 1) && fx);
+        sg0[a] = ng ? -1.f : 1.f;
+        sg1[a] = (ng != ((par & 4) != 0)) ? -1.f : 1.f;
+      }
+#pragma unroll
+      for (int j = 0; j < F::J; ++j)
+        if (F::row(t, j))
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const int k = t + R2 * j + R1 * k2;
+            const bool fz = k2 >= R2 / 2;  // k >= NN exactly when k2 >= R2/2 (compile time)
+            const int zo = fz ? M - k : k;
+            const float4* kp = (const float4*)(kq + zo * NARRP);
+            V kv[NARRP];
+#pragma unroll
+            for (int a2 = 0; a2 < NARRP / 2; ++a2) {
+              const float4 r = kp[a2];
+              kv[2 * a2] = make_float2(r.x, r.y);
+              kv[2 * a2 + 1] = make_float2(r.z, r.w);
+            }
+#pragma unroll
+            for (int a = 0; a < NARR; ++a)
+              if (sym_parity(MODE == KM_DIV ? 6 + a : a) != 0) kv[a] = (fz ? sg1[a] : sg0[a]) * kv[a];
+            const V x0 = X[0][j][k2], x1 = X[1][j][k2], x2 = X[2][j][k2];
+            const V p0 = ipx(x0), p1 = ipx(x1), p2 = ipx(x2);
+            // y += K x  ==  y + K.x x + K.y (i x), as packed f32x2 products
+            auto mac = [](V acc, V kk, V x, V ix) {
+              return __ffma2_rn(bcy2(kk), ix, __ffma2_rn(bcx2(kk), x, acc));
+            };
+            auto mul = [](V kk, V x, V ix) { return __ffma2_rn(bcy2(kk), ix, __fmul2_rn(bcx2(kk), x)); };
+            if (MODE == KM_DIV) {
+              X[0][j][k2] = mac(mac(mul(kv[0], x0, p0), kv[1], x1, p1), kv[2], x2, p2);
+            } else {
+              // symmetric 3x3: xx yy zz xy xz yz
+              X[0][j][k2] = mac(mac(mul(kv[0], x0, p0), kv[3], x1, p1), kv[4], x2, p2);
+              X[1][j][k2] = mac(mac(mul(kv[3], x0, p0), kv[1], x1, p1), kv[5], x2, p2);
+              X[2][j][k2] = mac(mac(mul(kv[4], x0, p0), kv[5], x1, p1), kv[2], x2, p2);
+            }
+          }
+    }
+    // ---- inverse z transforms, one component at a time through the line
+#pragma unroll
+    for (int c = 0; c < GO; ++c) {
+#pragma unroll
+      for (int j = 0; j < F::J; ++j) {
+        if (!F::row(t, j)) continue;
+        const int k1 = t + R2 * j;
+        Dft<R2, +1, T>::run(X[c][j]);
+        const float4* wr = (const float4*)(tw2 + k1 * (R1 == R2 ? TP1 : TP2));  // W^{k1 n2}, n2 pairs
+#pragma unroll
+        for (int n2 = 0; n2 < R2 / 2; ++n2) {
+          const float4 w = wr[n2];
+          if (n2 > 0) X[c][j][2 * n2] = cmulc(X[c][j][2 * n2], make_float2(w.x, w.y));
+          X[c][j][2 * n2 + 1] = cmulc(X[c][j][2 * n2 + 1], make_float2(w.z, w.w));
+        }
+      }
+      if (c > 0) line_sync();  // earlier readers of the line are done
+#pragma unroll
+      for (int j = 0; j < F::J; ++j) {
+        if (!F::row(t, j)) continue;
+        const int k1 = t + R2 * j;
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) s[n2 * PI + k1] = X[c][j][n2];
+      }
+      line_sync();
+      V u[R1];
+      const float4* row = (const float4*)(s + t * PI);
+#pragma unroll
+      for (int k1 = 0; k1 < R1 / 2; ++k1) {
+        const float4 r = row[k1];
+        u[2 * k1] = make_float2(r.x, r.y);
+        u[2 * k1 + 1] = make_float2(r.z, r.w);
+      }
+      dft_half_out<R1, +1, T>(u);
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) colbase[c * cs + (long long)(R2 * n1 + t) * zs] = u[n1];
+    }
+    line_sync();  // the line's last readers are done before the next tile writes it
+  }
+}
+
 // x-lines of all components: inverse, keep x < n, epilogue y = x + H u (or
 // y = u).  CO = 3 (one H block) or 6 ([J; M] with H_eps and H_mu, or [E; H]).
 template <typename T, int R1, int R2, int CO>
@@ -964,6 +1216,32 @@ struct FastPath {
       }
     }
   }
+  template <int MODE, int NP, int MINB>
+  static vie_status p3s(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
+    *done = false;
+    if constexpr (sizeof(T) != 4 || Fft2<T, R1, R2>::J * R2 > 16 || R1 > 16 || R2 % 2 != 0 ||
+                  !(MODE == KM_SYM3 || MODE == KM_DIV)) {
+      return VIE_OK;  // FP32 only; three components of a pencil must fit in registers
+    } else {
+      typedef P3sCfg<R1, R2, MODE, NP> Cfg;
+      constexpr int NTX = M / NP;
+      if constexpr (Cfg::NTHR > 1024 || NTX < 2) {
+        return VIE_OK;
+      } else {
+        if (2 * n != M) return VIE_OK;
+        const size_t sm = (size_t)Cfg::SMEM;
+        if (sm > smem_optin()) return VIE_OK;
+        auto kern = f_p3s<R1, R2, MODE, NP, MINB>;
+        // the whole unified L1 as shared memory: MINB CTAs of ~75 KB per SM
+        VIE_CK(allow_smem(kern, true));
+        const int groups = (M / 2 + 1) * (NTX / 2);
+        kern<<<dim3(groups, nrhs), Cfg::NTHR, sm, st>>>((float2*)B, n, C, (const float2*)K, (const float2*)tw);
+        VIE_CK(cudaGetLastError());
+        *done = true;
+        return VIE_OK;
+      }
+    }
+  }
   template <int MODE, int NP>
   static vie_status p3b_ok(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
     constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
@@ -992,7 +1270,10 @@ struct FastPath {
       case 8: return p3t<MODE, 4>(B, n, C, K, nrhs, tw, done, st);
       case 9: return p3t<MODE, 16>(B, n, C, K, nrhs, tw, done, st);
       case 10: return p3t<MODE, 8, true>(B, n, C, K, nrhs, tw, done, st);
-      default: return p3t<MODE, 4, true>(B, n, C, K, nrhs, tw, done, st);
+      case 11: return p3t<MODE, 4, true>(B, n, C, K, nrhs, tw, done, st);
+      case 12: return p3s<MODE, 8, 3>(B, n, C, K, nrhs, tw, done, st);
+      case 13: return p3s<MODE, 8, 2>(B, n, C, K, nrhs, tw, done, st);
+      default: return p3s<MODE, 4, 5>(B, n, C, K, nrhs, tw, done, st);
     }
   }
   // Run P3 variant `variant` (0..kP3Variants-1); *done = false if it does not apply to this shape.
@@ -1051,14 +1332,16 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
 // Autotuner for the z pass: every applicable variant (mirror-group CTAs with
 // 8, 16 or 4 pencils, one tile per CTA with 8 pencils, lane-pair
 // mirror-group CTAs with 8, 16 or 4 pencils, component-group mirror-group
-// CTAs with 8, 4 or 16 pencils, or component-group CTAs of 8 or 4 pencils
-// sized to the device, each walking several mirror groups) runs once untimed
+// CTAs with 8, 4 or 16 pencils, component-group CTAs of 8 or 4 pencils
+// sized to the device, each walking several mirror groups, or slim
+// component-group CTAs of 8 pencils for three or two CTAs per SM, or of 4
+// pencils for five) runs once untimed
 // (a pass over all candidates, which also brings the clocks up), then two
 // rounds of 3 launches timed with CUDA events on the buffer B (whose contents
 // are scratch at this point); each keeps its best round and the fastest is
 // kept for the problem's (precision, mode).  VIE_TUNE=0 takes the first
 // applicable variant; VIE_P3_VARIANT=k forces variant k.
-static const int kP3Variants = 12;
+static const int kP3Variants = 15;
 static const int kP3Generic = 99;
 
 template <typename T, int R1, int R2>

@@ -3,6 +3,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <string>
 
 #include "vie_internal.h"
@@ -10,6 +13,23 @@
 namespace vie {
 
 static thread_local std::string g_last_error;
+
+static std::mutex g_cfg_mutex;
+static std::set<std::pair<int, const void*>> g_cfg_done;
+
+bool kernel_configured(const void* kernel) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(g_cfg_mutex);
+  return g_cfg_done.count({dev, kernel}) != 0;
+}
+
+void kernel_mark_configured(const void* kernel) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(g_cfg_mutex);
+  g_cfg_done.insert({dev, kernel});
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -64,6 +84,9 @@ static void free_problem(vie_problem* P) {
   free_set(P->keval, st);
   cudaStreamSynchronize(st);
   for (cudaEvent_t e : P->prof.ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->arn_ev)
+    if (e) cudaEventDestroy(e);
+  if (P->arn_host) cudaFreeHost(P->arn_host);
   delete P;
 }
 

@@ -101,9 +101,13 @@ static const int kRedThreads = 256;
 // A sum of squares clamped at zero (rounding can leave it slightly negative),
 // with NaN kept: std::max(0.0, NaN) returns 0.0, which would turn a NaN
 // residual into a converged one and hide it from the non-finite checks.
-static inline double nonneg(double v) { return v < 0.0 ? 0.0 : v; }
+__host__ __device__ static inline double nonneg(double v) { return v < 0.0 ? 0.0 : v; }
 
 static const int kDotChunk = 8;
+static const int kArnSlots = 8;  // pinned state copies in flight (steps)
+static const int kArnLag = 2;    // steps the host may issue past the state it has read
+static_assert(kArnSlots == (int)(sizeof(((vie_problem*)nullptr)->arn_ev) / sizeof(cudaEvent_t)), "event slots");
+static_assert(kArnSlots > kArnLag + 1, "a slot is not reused while the host may still read it");
 // Blocks of a reduction over L elements: at least 8 elements per thread, so a
 // short vector does not pay for hundreds of idle blocks' reduction trees.
 static int red_blocks(long long L) {
@@ -205,84 +209,6 @@ __global__ void k_reduce_partials(const double2* __restrict__ partial, int k, in
   }
 }
 
-// w[r] -= sum_i coef[r * ldc + i] V_i[r]; block partial sums of |w[r]|^2 to
-// partial[r * ldp * G + block].  grid = (G, nb).
-template <typename TB>
-__global__ void __launch_bounds__(kRedThreads) k_axpy_norm(TB* __restrict__ w, const TB* __restrict__ V, long long ldi,
-                                                           int k, const double2* __restrict__ coef, int ldc,
-                                                           long long L, double2* partial, int ldp) {
-  typedef typename Acc<TB>::T AT;
-  __shared__ typename Acc<TB>::V cs[256];
-  __shared__ double red[kRedThreads / 32];
-  const int r = blockIdx.y;
-  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) {
-    cs[i].x = (AT)coef[(long long)r * ldc + i].x;
-    cs[i].y = (AT)coef[(long long)r * ldc + i].y;
-  }
-  __syncthreads();
-  TB* wr = w + (long long)r * L;
-  const TB* Vr = V + (long long)r * L;
-  AT nn = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
-    TB acc = wr[e];
-    AT sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
-    int i = 0;
-    for (; i + 4 <= k; i += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const TB v = Vr[(long long)(i + u) * ldi + e];
-        const typename Acc<TB>::V c = cs[i + u];
-        sx[u] += c.x * v.x - c.y * v.y;
-        sy[u] += c.x * v.y + c.y * v.x;
-      }
-    }
-    for (; i < k; ++i) {
-      const TB v = Vr[(long long)i * ldi + e];
-      const typename Acc<TB>::V c = cs[i];
-      sx[0] += c.x * v.x - c.y * v.y;
-      sy[0] += c.x * v.y + c.y * v.x;
-    }
-    acc.x -= (sx[0] + sx[1]) + (sx[2] + sx[3]);
-    acc.y -= (sy[0] + sy[1]) + (sy[2] + sy[3]);
-    wr[e] = acc;
-    nn += acc.x * acc.x + acc.y * acc.y;
-  }
-  for (int off = 16; off > 0; off >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)nn;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int j = 0; j < kRedThreads / 32; ++j) t += red[j];
-    partial[(long long)r * ldp * gridDim.x + blockIdx.x] = make_double2(t, 0.0);
-  }
-}
-
-// x[r] += sum_i coef[r * ldc + i] V_i[r]  (x FP64, products in TB's precision).  grid = (blocks, nb).
-template <typename TB>
-__global__ void k_update(double2* __restrict__ x, const TB* __restrict__ V, long long ldi, int k,
-                         const double2* __restrict__ coef, int ldc, long long L) {
-  typedef typename Acc<TB>::T AT;
-  __shared__ typename Acc<TB>::V cs[256];
-  const int r = blockIdx.y;
-  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) {
-    cs[i].x = (AT)coef[(long long)r * ldc + i].x;
-    cs[i].y = (AT)coef[(long long)r * ldc + i].y;
-  }
-  __syncthreads();
-  double2* xr = x + (long long)r * L;
-  const TB* Vr = V + (long long)r * L;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
-    AT ax = 0, ay = 0;
-    for (int i = 0; i < k; ++i) {
-      const TB v = Vr[(long long)i * ldi + e];
-      ax += cs[i].x * v.x - cs[i].y * v.y;
-      ay += cs[i].x * v.y + cs[i].y * v.x;
-    }
-    xr[e].x += (double)ax;
-    xr[e].y += (double)ay;
-  }
-}
-
 // dst[r] = scale[r] * src[r].  grid = (blocks, nb).  FP32 -> FP32 scales in
 // FP32 (FP64 conversions run on GB300's slow FP64 pipe); FP64 -> FP32 rounds
 // the FP64 product once.
@@ -319,18 +245,456 @@ __global__ void k_bminus(double2* __restrict__ r, const double2* __restrict__ b,
 
 static int ew_blocks(long long L) { return (int)std::min<long long>((L + 255) / 256, 152LL * 16); }
 
+// ------------------------------------------------ device-resident Arnoldi
+// A GMRES(m) cycle runs without a host round trip per step.  The basis is kept
+// unnormalised: slot i holds W_i with V_i = s_i W_i (s_i FP64, on the device),
+// so the apply of step j writes A W_j straight into slot j + 1 and no scaling
+// pass is needed.  Per step and group (lockstep right-hand sides, grid.y = member):
+//   apply        slot j+1 = A W_j
+//   k_arn_dots   (pass 0)  h_i = s_i s_j <W_i, A W_j>, |w|^2 = s_j^2 |A W_j|^2
+//   k_arn_axpy   (pass 0)  W_{j+1} -= sum_i (h_i s_i / s_j) W_i and |w'|^2; the
+//                          last block either asks for a second pass (|w'|^2 <
+//                          |w|^2 / 16, Kahan-Parlett "twice is enough") or
+//                          finalises the step
+//   k_arn_dots / k_arn_axpy (pass 1)  the second classical Gram-Schmidt pass;
+//                          their blocks return at entry unless it was asked for
+// Finalising (one thread) applies the earlier Givens rotations to the new
+// Hessenberg column, forms the next rotation, updates the residual estimate
+// |g_{j+1}|, sets s_{j+1} = s_j / h_{j+1,j}, and marks the member done when the
+// tolerance is reached, on breakdown (h_{j+1,j} = 0) or on a non-finite value.
+// Blocks of a member that is done return at entry.  Reductions finish in the
+// last block: each block stores its partial sums, fences, and counts itself in
+// with an atomic; the block that completes the count reads every partial
+// (bypassing L1), and resets the counter for the next kernel.
+struct ArnState {
+  int done;      // converged, breakdown, or non-finite
+  int steps;     // completed Arnoldi steps of this cycle
+  int reorth;    // the current step needs the second Gram-Schmidt pass
+  int nan;       // a non-finite value was met
+  double gabs;   // |g_steps|: the GMRES residual estimate
+  double stop;   // absolute stopping threshold of the cycle
+  double wn2;    // |w|^2 of the current step before projection
+  double beta;   // initial residual norm of the cycle
+};
+
+__host__ __device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double dnorm2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 dscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+// Device-side arrays of one group's Arnoldi state (carved from the Krylov workspace).
+struct ArnLayout {
+  int m = 0;
+  ArnState* st = nullptr;      // [nb]
+  double* sc = nullptr;        // [nb][m + 2] basis scale factors s_i
+  double2* R = nullptr;        // [nb][m][m + 1] rotated Hessenberg columns (upper triangle)
+  double2* cs = nullptr;       // [nb][m]
+  double2* sn = nullptr;       // [nb][m]
+  double2* gv = nullptr;       // [nb][m + 1] rotated right-hand side of the least squares
+  double2* hcol = nullptr;     // [nb][2][m + 2] coefficients of passes 0 and 1
+  double2* coef = nullptr;     // [nb][m] update coefficients y_i s_i
+  double2* partial = nullptr;  // [nb][m + 3][G] block partial sums
+  unsigned* cnt = nullptr;     // [nb] last-block counters
+};
+
+// Whether this block completes the member's reduction (call after storing partials).
+__device__ __forceinline__ bool arn_last_block(unsigned* cnt) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// Sum over blocks of partial[(r ldp + i) G + b] for i < k, one warp per i; the sum
+// of slot i replaces its block-0 entry (the only reader of slot i is this warp).
+__device__ __forceinline__ void arn_reduce(double2* partial, int r, int ldp, int G, int k) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < k; i += nw) {
+    double2* p = partial + ((long long)r * ldp + i) * G;
+    double2 sm = make_double2(0, 0);
+    for (int b = lane; b < G; b += 32) sm = sm + __ldcg(p + b);
+    for (int off = 16; off > 0; off >>= 1) {
+      sm.x += __shfl_down_sync(0xffffffffu, sm.x, off);
+      sm.y += __shfl_down_sync(0xffffffffu, sm.y, off);
+    }
+    __syncwarp();
+    if (lane == 0) p[0] = sm;
+  }
+  __syncthreads();
+}
+
+// Basis values moved per 16-byte access: two FP32 complex or one FP64 complex.
+template <typename TB> struct Pack;
+template <> struct Pack<float2> {
+  static constexpr int W = 2;
+  typedef float4 P;
+  static __device__ __forceinline__ float2 get(const float4& p, int q) {
+    return q == 0 ? make_float2(p.x, p.y) : make_float2(p.z, p.w);
+  }
+  static __device__ __forceinline__ void put(float4& p, int q, float2 v) {
+    if (q == 0) { p.x = v.x; p.y = v.y; } else { p.z = v.x; p.w = v.y; }
+  }
+};
+template <> struct Pack<double2> {
+  static constexpr int W = 1;
+  typedef double2 P;
+  static __device__ __forceinline__ double2 get(const double2& p, int) { return p; }
+  static __device__ __forceinline__ void put(double2& p, int, double2 v) { p = v; }
+};
+
+// Pass p: block partials of <W_i, W_{j+1}>, i <= j (pass 0 also |W_{j+1}|^2); the last
+// block stores h_i = s_i s_j <W_i, W_{j+1}> and (pass 0) |w|^2 = s_j^2 |W_{j+1}|^2.
+// Vectors are read in 16-byte packs, two packs in flight per thread; ldi and L
+// are multiples of the pack width except for an odd tail handled element-wise.
+template <typename TB>
+__global__ void __launch_bounds__(kRedThreads) k_arn_dots(const TB* __restrict__ V, long long ldi, int j, long long L,
+                                                          ArnLayout A, int pass) {
+  typedef typename Acc<TB>::T AT;
+  typedef Pack<TB> PK;
+  typedef typename PK::P P;
+  constexpr int W = PK::W;
+  __shared__ double2 red[kRedThreads / 32][kDotChunk];
+  const int r = blockIdx.y, G = gridDim.x, m = A.m, ldp = m + 3;
+  ArnState* S = A.st + r;
+  if (S->done || (pass == 1 && !S->reorth)) return;  // block-uniform
+  const TB* Vr = V + (long long)r * L;
+  const TB* wr = V + (long long)(j + 1) * ldi + (long long)r * L;
+  const int k = j + 1, ktot = k + (pass == 0 ? 1 : 0);
+  // packs when every vector start is pack-aligned (ldi, L multiples of W), else element-wise
+  const bool packed = (W > 1) && (ldi % W == 0) && (L % W == 0);
+  const long long NP = packed ? L / W : 0;  // packs per vector
+  const long long stride = (long long)G * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (int i0 = 0; i0 < ktot; i0 += kDotChunk) {
+    const int cnt = min(kDotChunk, ktot - i0);
+    AT ar[kDotChunk], ai[kDotChunk];
+#pragma unroll
+    for (int t = 0; t < kDotChunk; ++t) ar[t] = ai[t] = (AT)0;
+    auto acc1 = [&](int t, TB v, TB we) {
+      ar[t] += v.x * we.x + v.y * we.y;
+      ai[t] += v.x * we.y - v.y * we.x;
+    };
+    if (packed) {
+      const P* wp = (const P*)wr;
+      long long e = tid;
+      for (; e + stride < NP; e += 2 * stride) {
+        const P wa = wp[e], wb = wp[e + stride];
+#pragma unroll
+        for (int t = 0; t < kDotChunk; ++t)
+          if (t < cnt) {
+            const int i = i0 + t;
+            const P va = (i < k) ? ((const P*)(Vr + (long long)i * ldi))[e] : wa;
+            const P vb = (i < k) ? ((const P*)(Vr + (long long)i * ldi))[e + stride] : wb;
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+              acc1(t, PK::get(va, q), PK::get(wa, q));
+              acc1(t, PK::get(vb, q), PK::get(wb, q));
+            }
+          }
+      }
+      for (; e < NP; e += stride) {
+        const P wa = wp[e];
+#pragma unroll
+        for (int t = 0; t < kDotChunk; ++t)
+          if (t < cnt) {
+            const int i = i0 + t;
+            const P va = (i < k) ? ((const P*)(Vr + (long long)i * ldi))[e] : wa;
+#pragma unroll
+            for (int q = 0; q < W; ++q) acc1(t, PK::get(va, q), PK::get(wa, q));
+          }
+      }
+    } else {
+      for (long long e = tid; e < L; e += stride) {
+        const TB we = wr[e];
+#pragma unroll
+        for (int t = 0; t < kDotChunk; ++t)
+          if (t < cnt) {
+            const int i = i0 + t;
+            acc1(t, (i < k) ? Vr[(long long)i * ldi + e] : we, we);
+          }
+      }
+    }
+    // warp sums in the accumulation type (slots in use only), cross-warp in FP64
+#pragma unroll
+    for (int t = 0; t < kDotChunk; ++t)
+      if (t < cnt) {
+        AT ax = ar[t], ay = ai[t];
+        for (int off = 16; off > 0; off >>= 1) {
+          ax += __shfl_down_sync(0xffffffffu, ax, off);
+          ay += __shfl_down_sync(0xffffffffu, ay, off);
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = make_double2((double)ax, (double)ay);
+      }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double2 sm = make_double2(0, 0);
+      for (int w = 0; w < kRedThreads / 32; ++w) sm = sm + red[w][threadIdx.x];
+      A.partial[((long long)r * ldp + i0 + threadIdx.x) * G + blockIdx.x] = sm;
+    }
+    __syncthreads();
+  }
+  if (!arn_last_block(A.cnt + r)) return;
+  arn_reduce(A.partial, r, ldp, G, ktot);
+  if (threadIdx.x == 0) A.cnt[r] = 0;
+  const double* sc = A.sc + (long long)r * (m + 2);
+  double2* h = A.hcol + ((long long)r * 2 + pass) * (m + 2);
+  const double sj = sc[j];
+  for (int i = threadIdx.x; i < ktot; i += blockDim.x) {
+    const double2 raw = A.partial[((long long)r * ldp + i) * G];
+    if (i < k) h[i] = dscale(sc[i] * sj, raw);
+    else S->wn2 = sj * sj * raw.x;
+  }
+}
+
+// Finalise step j of member r (one thread): Hessenberg column h (i <= j) and
+// h_{j+1,j} = hn; rotations, residual estimate, next scale, done flag.
+__device__ void arn_finalize(ArnLayout& A, int r, int j, const double2* h0, const double2* h1, double hn) {
+  const int m = A.m;
+  ArnState* S = A.st + r;
+  double2* Rc = A.R + ((long long)r * m + j) * (m + 1);
+  double2* cs = A.cs + (long long)r * m;
+  double2* sn = A.sn + (long long)r * m;
+  double2* g = A.gv + (long long)r * (m + 1);
+  double* sc = A.sc + (long long)r * (m + 2);
+  bool finite = isfinite(hn) && isfinite(S->wn2);
+  for (int i = 0; i <= j; ++i) {
+    double2 v = h0[i];
+    if (h1) v = v + h1[i];
+    finite = finite && isfinite(v.x) && isfinite(v.y);
+    Rc[i] = v;
+  }
+  if (!finite) {
+    S->nan = 1;
+    S->done = 1;
+    return;
+  }
+  // earlier rotations G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]] on rows i, i+1
+  for (int i = 0; i < j; ++i) {
+    const double2 a = Rc[i], b = Rc[i + 1];
+    Rc[i] = cmul(dconj(cs[i]), a) + cmul(dconj(sn[i]), b);
+    Rc[i + 1] = cmul(cs[i], b) - cmul(sn[i], a);
+  }
+  const double2 a = Rc[j];
+  const double den = sqrt(dnorm2(a) + hn * hn);
+  const double2 c = den > 0 ? dscale(1.0 / den, a) : make_double2(1, 0);
+  const double2 sv = den > 0 ? make_double2(hn / den, 0) : make_double2(0, 0);
+  cs[j] = c;
+  sn[j] = sv;
+  Rc[j] = cmul(dconj(c), a) + dscale(hn, dconj(sv));
+  const double2 gj = g[j];
+  g[j + 1] = dscale(-1.0, cmul(sv, gj));
+  g[j] = cmul(dconj(c), gj);
+  S->steps = j + 1;
+  S->gabs = sqrt(dnorm2(g[j + 1]));
+  S->reorth = 0;
+  if (S->gabs <= S->stop || hn == 0.0) {
+    S->done = 1;
+  } else {
+    sc[j + 1] = sc[j] / hn;
+  }
+}
+
+// Pass p: W_{j+1} -= sum_{i <= j} (h_i s_i / s_j) W_i and block partials of |W_{j+1}|^2;
+// the last block decides on the second pass (pass 0) or finalises the step.
+template <typename TB>
+__global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, long long ldi, int j, long long L,
+                                                          ArnLayout A, int pass) {
+  typedef typename Acc<TB>::T AT;
+  __shared__ typename Acc<TB>::V cf[256];
+  __shared__ double red[kRedThreads / 32];
+  const int r = blockIdx.y, G = gridDim.x, m = A.m, ldp = m + 3;
+  ArnState* S = A.st + r;
+  if (S->done || (pass == 1 && !S->reorth)) return;  // block-uniform
+  const double* sc = A.sc + (long long)r * (m + 2);
+  const double2* h = A.hcol + ((long long)r * 2 + pass) * (m + 2);
+  const int k = j + 1;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double f = sc[i] / sc[j];
+    cf[i].x = (AT)(h[i].x * f);
+    cf[i].y = (AT)(h[i].y * f);
+  }
+  __syncthreads();
+  const TB* Vr = V + (long long)r * L;
+  TB* wr = V + (long long)(j + 1) * ldi + (long long)r * L;
+  AT nn = 0;
+  typedef Pack<TB> PK;
+  typedef typename PK::P P;
+  constexpr int W = PK::W;
+  const bool packed = (W > 1) && (ldi % W == 0) && (L % W == 0);
+  const long long NPK = packed ? L / W : L;  // units (packs or elements) per vector
+  const long long stride = (long long)G * blockDim.x;
+  // one unit: W elements of W_{j+1} at unit e, minus the projection, and its |.|^2
+  auto unit = [&](long long e) {
+    TB acc[W];
+    P pw;
+    if (packed) {
+      pw = ((const P*)wr)[e];
+#pragma unroll
+      for (int q = 0; q < W; ++q) acc[q] = PK::get(pw, q);
+    } else {
+      acc[0] = wr[e];
+    }
+    AT sx[W][2], sy[W][2];
+#pragma unroll
+    for (int q = 0; q < W; ++q) sx[q][0] = sx[q][1] = sy[q][0] = sy[q][1] = 0;
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const typename Acc<TB>::V c = cf[i + u];
+        if (packed) {
+          const P pv = ((const P*)(Vr + (long long)(i + u) * ldi))[e];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            const TB v = PK::get(pv, q);
+            sx[q][u] += c.x * v.x - c.y * v.y;
+            sy[q][u] += c.x * v.y + c.y * v.x;
+          }
+        } else {
+          const TB v = Vr[(long long)(i + u) * ldi + e];
+          sx[0][u] += c.x * v.x - c.y * v.y;
+          sy[0][u] += c.x * v.y + c.y * v.x;
+        }
+      }
+    }
+    if (i < k) {
+      const typename Acc<TB>::V c = cf[i];
+      if (packed) {
+        const P pv = ((const P*)(Vr + (long long)i * ldi))[e];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          const TB v = PK::get(pv, q);
+          sx[q][0] += c.x * v.x - c.y * v.y;
+          sy[q][0] += c.x * v.y + c.y * v.x;
+        }
+      } else {
+        const TB v = Vr[(long long)i * ldi + e];
+        sx[0][0] += c.x * v.x - c.y * v.y;
+        sy[0][0] += c.x * v.y + c.y * v.x;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (q == 0 || packed) {
+        acc[q].x -= sx[q][0] + sx[q][1];
+        acc[q].y -= sy[q][0] + sy[q][1];
+        nn += acc[q].x * acc[q].x + acc[q].y * acc[q].y;
+      }
+    if (packed) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) PK::put(pw, q, acc[q]);
+      ((P*)wr)[e] = pw;
+    } else {
+      wr[e] = acc[0];
+    }
+  };
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NPK; e += stride) unit(e);
+  for (int off = 16; off > 0; off >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < kRedThreads / 32; ++w) t += red[w];
+    A.partial[((long long)r * ldp + m + 2) * G + blockIdx.x] = make_double2(t, 0.0);
+  }
+  if (!arn_last_block(A.cnt + r)) return;
+  if (threadIdx.x < 32) {
+    double t = 0;
+    for (int b = threadIdx.x; b < G; b += 32) t += __ldcg(&A.partial[((long long)r * ldp + m + 2) * G + b]).x;
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (threadIdx.x == 0) {
+      A.cnt[r] = 0;
+      const double nw2 = nonneg(sc[j] * sc[j] * t);  // |w'|^2 at true scale
+      const double2* h0 = A.hcol + (long long)r * 2 * (m + 2);
+      if (pass == 0 && nw2 < 0.0625 * S->wn2) {
+        S->reorth = 1;  // the second pass finalises
+      } else {
+        arn_finalize(A, r, j, h0, pass == 1 ? h0 + (m + 2) : nullptr, sqrt(nw2));
+      }
+    }
+  }
+}
+
+// Start of a cycle: state of member r from its residual norm beta and threshold.
+__global__ void k_arn_init(ArnLayout A, const double* __restrict__ init, int nb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  const int m = A.m;
+  const double beta = init[2 * r], stop = init[2 * r + 1];
+  ArnState* S = A.st + r;
+  S->done = (beta <= stop || beta == 0.0) ? 1 : 0;
+  S->steps = 0;
+  S->reorth = 0;
+  S->nan = isfinite(beta) ? 0 : 1;
+  S->gabs = beta;
+  S->stop = stop;
+  S->wn2 = 0.0;
+  S->beta = beta;
+  A.sc[(long long)r * (m + 2)] = 1.0;
+  double2* g = A.gv + (long long)r * (m + 1);
+  g[0] = make_double2(beta, 0.0);
+  A.cnt[r] = 0;
+}
+
+// End of a cycle: back substitution R y = g (k = steps) and coef_i = y_i s_i, one thread per member.
+__global__ void k_arn_solve(ArnLayout A, int nb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  const int m = A.m, k = A.st[r].steps;
+  const double2* g = A.gv + (long long)r * (m + 1);
+  const double* sc = A.sc + (long long)r * (m + 2);
+  double2* y = A.coef + (long long)r * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 acc = g[i];
+    for (int q = i + 1; q < k; ++q) acc = acc - cmul(A.R[((long long)r * m + q) * (m + 1) + i], y[q]);
+    const double2 d = A.R[((long long)r * m + i) * (m + 1) + i];
+    const double dd = dnorm2(d);
+    y[i] = dscale(1.0 / dd, cmul(acc, dconj(d)));
+  }
+  for (int i = 0; i < k; ++i) y[i] = dscale(sc[i], y[i]);
+}
+
+// x[r] += sum_{i < steps[r]} coef[r][i] W_i[r]  (x FP64, products in TB's precision).  grid = (blocks, nb).
+template <typename TB>
+__global__ void k_arn_update(double2* __restrict__ x, const TB* __restrict__ V, long long ldi, ArnLayout A,
+                             long long L) {
+  typedef typename Acc<TB>::T AT;
+  __shared__ typename Acc<TB>::V cs[256];
+  const int r = blockIdx.y, m = A.m;
+  const int k = min(A.st[r].steps, 256);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    cs[i].x = (AT)A.coef[(long long)r * m + i].x;
+    cs[i].y = (AT)A.coef[(long long)r * m + i].y;
+  }
+  __syncthreads();
+  if (k == 0) return;
+  double2* xr = x + (long long)r * L;
+  const TB* Vr = V + (long long)r * L;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
+    AT ax = 0, ay = 0;
+    for (int i = 0; i < k; ++i) {
+      const TB v = Vr[(long long)i * ldi + e];
+      ax += cs[i].x * v.x - cs[i].y * v.y;
+      ay += cs[i].x * v.y + cs[i].y * v.x;
+    }
+    xr[e].x += (double)ax;
+    xr[e].y += (double)ay;
+  }
+}
+
 struct Group {
   int nb = 1;
   int m = 1;
   long long L = 0;
-  double2* partial = nullptr;  // [nb][m+3][G]
+  double2* partial = nullptr;  // [nb][m+3][G] (norms of the outer loop)
   double2* hdev = nullptr;     // [nb][HS]
-  double* sdev = nullptr;      // [nb] scales
   double2* r = nullptr;        // [nb][L] FP64
-  double2* w64 = nullptr;      // [nb][L]
-  float2* w32 = nullptr;       // [nb][L]
-  void* V = nullptr;           // [m+1][nb][L]
+  void* V = nullptr;           // [m+1][nb][L] unnormalised basis W_i
   int HS = 0;                  // stride of hdev per rhs
+  ArnLayout A;
+  double* init = nullptr;      // [nb][2] device: beta, stop per member
 };
 
 static int ldp_of(const Group& g) { return g.m + 3; }
@@ -350,152 +714,136 @@ static vie_status norms_host(const double2* v, Group& g, std::vector<double>& ou
   return VIE_OK;
 }
 
+// Pinned host mirror of the group's per-member state, one slot per step in flight.
+static vie_status ensure_mirror(vie_problem* P, int nb) {
+  const size_t need = sizeof(ArnState) * (size_t)nb * kArnSlots;
+  if (P->arn_host_bytes < need) {
+    if (P->arn_host) cudaFreeHost(P->arn_host);
+    P->arn_host = nullptr;
+    P->arn_host_bytes = 0;
+    VIE_CK(cudaMallocHost(&P->arn_host, need));
+    P->arn_host_bytes = need;
+  }
+  for (int i = 0; i < kArnSlots; ++i)
+    if (!P->arn_ev[i]) VIE_CK(cudaEventCreateWithFlags(&P->arn_ev[i], cudaEventDisableTiming));
+  return VIE_OK;
+}
+
 // One GMRES(m) cycle for the whole group on the operator applied in the
-// precision of TB (basis type TB).  Arnoldi: classical Gram-Schmidt, one
-// device reduction per step (inner products and |w|^2 in one pass, the update
-// and |w'|^2 in a second), a second Gram-Schmidt pass when the first removed
-// more than 3/4 of some member's norm (Kahan-Parlett "twice is enough").
-//   r (FP64 residuals, norms beta[r]); x (FP64) += V y.  Members with
-//   beta = 0 ride along with zero vectors.  Returns steps per member.
+// precision of TB (basis type TB), device-resident (see above).  r holds the
+// FP64 residuals with norms beta[r]; x (FP64) += V y.  Members with beta = 0 or
+// beta <= stop are done from the start.  Returns the steps of each member.
 template <typename TB>
 static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double>& beta, double2* x,
                               const std::vector<double>& stop_abs, std::vector<int>& steps, int* applies,
                               cudaStream_t st) {
   const long long L = g.L;
-  const int nb = g.nb, m = g.m, HS = g.HS, ldp = ldp_of(g);
+  const int nb = g.nb, m = g.m;
   const long long ldi = (long long)nb * L;
   TB* V = (TB*)g.V;
-  TB* w = (TB*)(sizeof(TB) == sizeof(double2) ? (void*)g.w64 : (void*)g.w32);
   const int prec = sizeof(TB) == sizeof(double2) ? VIE_FP64 : VIE_FP32;
   const int G = red_blocks(L);
   const dim3 ewg(ew_blocks(L), nb), redg(G, nb);
-  std::vector<double> sc(nb);
-  for (int r = 0; r < nb; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
-  VIE_CK(cudaMemcpyAsync(g.sdev, sc.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
-  k_scale<TB, double2><<<ewg, 256, 0, st>>>(V, g.r, g.sdev, L);
-  VIE_CK(cudaGetLastError());
-  std::vector<cd> Hm((size_t)nb * (m + 1) * m, cd(0, 0)), cs((size_t)nb * m), sn((size_t)nb * m),
-      gg((size_t)nb * (m + 1), cd(0, 0));
-  std::vector<char> done(nb, 0);
-  steps.assign(nb, 0);
+  vie_status s = ensure_mirror(P, nb);
+  if (s != VIE_OK) return s;
+  ArnState* mirror = (ArnState*)P->arn_host;
+  ArnLayout A = g.A;
+  A.m = m;
+  // W_0 = r / beta (s_0 = 1), and the cycle's initial state
+  std::vector<double> sc(nb), init(2 * (size_t)nb);
   int active = 0;
   for (int r = 0; r < nb; ++r) {
-    gg[(size_t)r * (m + 1)] = beta[r];
-    if (beta[r] <= stop_abs[r] || beta[r] == 0.0) done[r] = 1;
-    else ++active;
+    sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+    init[2 * r] = beta[r];
+    init[2 * r + 1] = stop_abs[r];
+    if (!(beta[r] <= stop_abs[r] || beta[r] == 0.0)) ++active;
   }
-  std::vector<double2> hb((size_t)nb * HS);
-  const int H2 = m + 3;  // second-pass slot offset inside a member's hdev row
-  for (int j = 0; j < m && active > 0; ++j) {
-    vie_status s = run_apply(P, P->kapply, V + (long long)j * ldi, w, prec, nb, true, st);
-    if (s != VIE_OK) return s;
-    *applies += active;
-    k_multidot<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j + 1, w, L, g.partial, ldp, 1);
-    VIE_CK(cudaGetLastError());
-    k_reduce_partials<<<dim3(j + 2, nb), 256, 0, st>>>(g.partial, j + 2, G, ldp, g.hdev, HS);
-    VIE_CK(cudaGetLastError());
-    k_axpy_norm<TB><<<redg, kRedThreads, 0, st>>>(w, V, ldi, j + 1, g.hdev, HS, L, g.partial, ldp);
-    VIE_CK(cudaGetLastError());
-    k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, G, ldp, g.hdev + (j + 2), HS);
-    VIE_CK(cudaGetLastError());
-    VIE_CK(cudaMemcpyAsync(hb.data(), g.hdev, sizeof(double2) * nb * HS, cudaMemcpyDeviceToHost, st));
-    VIE_CK(cudaStreamSynchronize(st));
-    bool reorth = false;
-    for (int r = 0; r < nb; ++r)
-      if (!done[r] && hb[(size_t)r * HS + j + 2].x < 0.0625 * hb[(size_t)r * HS + j + 1].x) reorth = true;
-    if (reorth) {
-      k_multidot<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j + 1, w, L, g.partial, ldp, 0);
-      VIE_CK(cudaGetLastError());
-      k_reduce_partials<<<dim3(j + 1, nb), 256, 0, st>>>(g.partial, j + 1, G, ldp, g.hdev + H2, HS);
-      VIE_CK(cudaGetLastError());
-      k_axpy_norm<TB><<<redg, kRedThreads, 0, st>>>(w, V, ldi, j + 1, g.hdev + H2, HS, L, g.partial, ldp);
-      VIE_CK(cudaGetLastError());
-      k_reduce_partials<<<dim3(1, nb), 256, 0, st>>>(g.partial, 1, G, ldp, g.hdev + H2 + j + 1, HS);
-      VIE_CK(cudaGetLastError());
-      VIE_CK(cudaMemcpyAsync(hb.data(), g.hdev, sizeof(double2) * nb * HS, cudaMemcpyDeviceToHost, st));
-      VIE_CK(cudaStreamSynchronize(st));
-    }
-    for (int r = 0; r < nb; ++r) {
-      sc[r] = 0.0;
-      if (done[r]) continue;
-      const double2* hr = &hb[(size_t)r * HS];
-      const double w0 = hr[j + 1].x;
-      double wn2 = reorth ? hr[H2 + j + 1].x : hr[j + 2].x;
-      const double hn = std::sqrt(nonneg(wn2));
-      if (!std::isfinite(hn) || !std::isfinite(w0)) {
-        set_error("non-finite value in the Arnoldi process");
-        return VIE_ENAN;
-      }
-      cd* H = &Hm[(size_t)r * (m + 1) * m];
-      cd* c_ = &cs[(size_t)r * m];
-      cd* s_ = &sn[(size_t)r * m];
-      cd* g_ = &gg[(size_t)r * (m + 1)];
-      for (int i = 0; i <= j; ++i) {
-        cd h(hr[i].x, hr[i].y);
-        if (reorth) h += cd(hr[H2 + i].x, hr[H2 + i].y);
-        H[(size_t)i * m + j] = h;
-      }
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const cd a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = std::conj(c_[i]) * a + std::conj(s_[i]) * bb;
-        H[(size_t)(i + 1) * m + j] = -s_[i] * a + c_[i] * bb;
-      }
-      const cd a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
-      const double den = std::sqrt(std::norm(a) + std::norm(bb));
-      c_[j] = den > 0 ? a / den : cd(1, 0);
-      s_[j] = den > 0 ? bb / den : cd(0, 0);
-      H[(size_t)j * m + j] = std::conj(c_[j]) * a + std::conj(s_[j]) * bb;
-      H[(size_t)(j + 1) * m + j] = 0;
-      g_[j + 1] = -s_[j] * g_[j];
-      g_[j] = std::conj(c_[j]) * g_[j];
-      steps[r] = j + 1;
-      if (std::abs(g_[j + 1]) <= stop_abs[r] || hn == 0.0) {
-        done[r] = 1;
-        --active;
-      } else {
-        sc[r] = 1.0 / hn;
-      }
-    }
-    if (j + 1 < m && active > 0) {
-      VIE_CK(cudaMemcpyAsync(g.sdev, sc.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
-      k_scale<TB, TB><<<ewg, 256, 0, st>>>(V + (long long)(j + 1) * ldi, w, g.sdev, L);
-      VIE_CK(cudaGetLastError());
-    }
-  }
-  // back substitution R y = g per member; coefficients to the device, x += V y
-  int kmax = 0;
-  for (int r = 0; r < nb; ++r) kmax = std::max(kmax, steps[r]);
-  if (kmax == 0) return VIE_OK;
-  std::vector<cd> y((size_t)nb * HS, cd(0, 0));
-  for (int r = 0; r < nb; ++r) {
-    const int jr = steps[r];
-    const cd* H = &Hm[(size_t)r * (m + 1) * m];
-    const cd* g_ = &gg[(size_t)r * (m + 1)];
-    cd* yr = &y[(size_t)r * HS];
-    for (int i = jr - 1; i >= 0; --i) {
-      cd acc = g_[i];
-      for (int q = i + 1; q < jr; ++q) acc -= H[(size_t)i * m + q] * yr[q];
-      yr[i] = acc / H[(size_t)i * m + i];
-    }
-  }
-  VIE_CK(cudaMemcpyAsync(g.hdev, y.data(), sizeof(double2) * nb * HS, cudaMemcpyHostToDevice, st));
-  k_update<TB><<<ewg, 256, 0, st>>>(x, V, ldi, kmax, g.hdev, HS, L);
+  VIE_CK(cudaMemcpyAsync(g.hdev, sc.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+  VIE_CK(cudaMemcpyAsync(g.init, init.data(), sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, st));
+  k_scale<TB, double2><<<ewg, 256, 0, st>>>(V, g.r, (const double*)g.hdev, L);
   VIE_CK(cudaGetLastError());
-  VIE_CK(cudaStreamSynchronize(st));  // y is a host temporary
+  k_arn_init<<<(nb + 63) / 64, 64, 0, st>>>(A, g.init, nb);
+  VIE_CK(cudaGetLastError());
+  // (copies from pageable memory have left sc and init by the time they return)
+  steps.assign(nb, 0);
+  if (active == 0) return VIE_OK;
+  // The host runs at most kArnLag steps ahead of the state it has read; when the
+  // residual estimates predict convergence within that lag it waits for the
+  // latest step instead, so few steps are issued after every member is done.
+  std::vector<ArnState> cur, prev;  // the latest state read, and the one before it
+  auto all_done = [&](const std::vector<ArnState>& ms) {
+    for (int r = 0; r < nb; ++r)
+      if (!ms[r].done) return false;
+    return true;
+  };
+  auto near_done = [&]() {
+    if (cur.empty() || prev.empty()) return false;
+    for (int r = 0; r < nb; ++r) {
+      if (cur[r].done) continue;
+      const int ds = cur[r].steps - prev[r].steps;
+      if (ds <= 0 || !(prev[r].gabs > 0) || !(cur[r].gabs > 0)) return true;
+      const double rate = std::pow(cur[r].gabs / prev[r].gabs, 1.0 / ds);
+      if (!(rate < 1.0)) return true;
+      const double need = std::log(cur[r].stop / cur[r].gabs) / std::log(rate);
+      if (need <= kArnLag + 1) return true;
+    }
+    return false;
+  };
+  int read_step = -1;
+  for (int j = 0; j < m; ++j) {
+    // read back the state of step j - kArnLag, or of step j - 1 near convergence
+    int want = near_done() ? j - 1 : j - kArnLag;
+    if (want > read_step) {
+      VIE_CK(cudaEventSynchronize(P->arn_ev[want % kArnSlots]));
+      const ArnState* ms = mirror + (size_t)(want % kArnSlots) * nb;
+      prev.swap(cur);
+      cur.assign(ms, ms + nb);
+      read_step = want;
+      if (all_done(cur)) break;
+    }
+    s = run_apply(P, P->kapply, V + (long long)j * ldi, V + (long long)(j + 1) * ldi, prec, nb, true, st);
+    if (s != VIE_OK) return s;
+    for (int pass = 0; pass < 2; ++pass) {
+      k_arn_dots<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j, L, A, pass);
+      VIE_CK(cudaGetLastError());
+      k_arn_axpy<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j, L, A, pass);
+      VIE_CK(cudaGetLastError());
+    }
+    VIE_CK(cudaMemcpyAsync(mirror + (size_t)(j % kArnSlots) * nb, A.st, sizeof(ArnState) * nb,
+                           cudaMemcpyDeviceToHost, st));
+    VIE_CK(cudaEventRecord(P->arn_ev[j % kArnSlots], st));
+  }
+  // back substitution and x += V y on the device; the final state to the host
+  k_arn_solve<<<(nb + 63) / 64, 64, 0, st>>>(A, nb);
+  VIE_CK(cudaGetLastError());
+  k_arn_update<TB><<<ewg, 256, 0, st>>>(x, V, ldi, A, L);
+  VIE_CK(cudaGetLastError());
+  std::vector<ArnState> fin(nb);
+  VIE_CK(cudaMemcpyAsync(fin.data(), A.st, sizeof(ArnState) * nb, cudaMemcpyDeviceToHost, st));
+  VIE_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nb; ++r) {
+    if (fin[r].nan) {
+      set_error("non-finite value in the Arnoldi process");
+      return VIE_ENAN;
+    }
+    steps[r] = fin[r].steps;
+    *applies += fin[r].steps;
+  }
   return VIE_OK;
 }
 
 // Bytes of Krylov workspace per right-hand side.
 static size_t group_bytes_per_rhs(long long L, int m, bool mixed) {
   const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
-  return esz * (size_t)(m + 1) * L + sizeof(double2) * 2 * L + sizeof(float2) * L +
-         sizeof(double2) * ((size_t)(m + 3) * kRedBlocks + 2 * (m + 4)) + 64;
+  const size_t arn = sizeof(ArnState) + sizeof(double) * (m + 2) + sizeof(double2) * ((size_t)m * (m + 1) + 2 * m +
+                     (m + 1) + 2 * (m + 2) + m) + sizeof(unsigned) + 2 * sizeof(double);
+  return esz * (size_t)(m + 1) * L + sizeof(double2) * L + sizeof(double2) * ((size_t)(m + 3) * kRedBlocks +
+         2 * (m + 4)) + arn + 16 * 256;
 }
 
 static vie_status ensure_group(vie_problem* P, int m, bool mixed, int nb, Group& g, cudaStream_t st) {
   const long long L = (long long)P->ncomp * P->n * P->n * P->n;
-  const size_t need = group_bytes_per_rhs(L, m, mixed) * nb + 16 * 4096;
+  const size_t need = group_bytes_per_rhs(L, m, mixed) * nb + 32 * 4096;
   if (P->ks.bytes < need) {
     dfree(P->ks.buf, st);
     P->ks.buf = nullptr;
@@ -520,10 +868,19 @@ static vie_status ensure_group(vie_problem* P, int m, bool mixed, int nb, Group&
   g.HS = 2 * (m + 4);
   g.partial = (double2*)take(sizeof(double2) * (size_t)nb * (m + 3) * kRedBlocks);
   g.hdev = (double2*)take(sizeof(double2) * (size_t)nb * g.HS);
-  g.sdev = (double*)take(sizeof(double) * nb);
+  g.init = (double*)take(sizeof(double) * 2 * (size_t)nb);
+  g.A.m = m;
+  g.A.st = (ArnState*)take(sizeof(ArnState) * (size_t)nb);
+  g.A.sc = (double*)take(sizeof(double) * (size_t)nb * (m + 2));
+  g.A.R = (double2*)take(sizeof(double2) * (size_t)nb * m * (m + 1));
+  g.A.cs = (double2*)take(sizeof(double2) * (size_t)nb * m);
+  g.A.sn = (double2*)take(sizeof(double2) * (size_t)nb * m);
+  g.A.gv = (double2*)take(sizeof(double2) * (size_t)nb * (m + 1));
+  g.A.hcol = (double2*)take(sizeof(double2) * (size_t)nb * 2 * (m + 2));
+  g.A.coef = (double2*)take(sizeof(double2) * (size_t)nb * m);
+  g.A.partial = g.partial;
+  g.A.cnt = (unsigned*)take(sizeof(unsigned) * (size_t)nb);
   g.r = (double2*)take(sizeof(double2) * (size_t)nb * L);
-  g.w64 = (double2*)take(sizeof(double2) * (size_t)nb * L);
-  g.w32 = (float2*)take(sizeof(float2) * (size_t)nb * L);
   g.V = take(esz * (size_t)(m + 1) * nb * L);
   return VIE_OK;
 }

@@ -407,6 +407,8 @@ template <int S, typename T> struct Dft<16, S, T> {
         const int j = r2 * q1;  // w16^(r2 q1)
         if (j == 0) {
           a[q1][r2] = t[q1];
+        } else if (j == 4) {  // w16^4 = S i: a swap, no multiply
+          a[q1][r2] = mul_si<S>(t[q1]);
         } else {
           const T c = (T)cos_pi8(j);
           const T s = (T)(S * cos_pi8(j + 12));  // sin(pi j/8) = cos(pi (j - 4)/8) = cos(pi (j+12)/8)

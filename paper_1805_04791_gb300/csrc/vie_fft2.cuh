@@ -94,11 +94,16 @@ __device__ __forceinline__ typename CT<T>::V twc(typename CT<T>::V a, int j) {
   double c, s;
   if constexpr (32 % R == 0) {
     const int q = (j * (32 / R)) & 31;  // angle pi q / 16
+    // quarter turns are exact swaps and negations (j is a constant in every caller)
+    if (q == 8) return mul_si<S>(a);
+    if (q == 24) return mul_si<-S>(a);
     c = cos_pi16(q);
     s = S * cos_pi16(q + 24);  // sin(pi q/16) = cos(pi (q - 8)/16)
   } else {
     static_assert(24 % R == 0, "twiddle table covers R | 32 and R | 24");
     const int q = (j * (24 / R)) % 24;  // angle 2 pi q / 24
+    if (q == 6) return mul_si<S>(a);
+    if (q == 18) return mul_si<-S>(a);
     c = cos_2pi24(q);
     s = S * cos_2pi24(q + 18);  // sin(t) = cos(t - pi/2)
   }

@@ -91,6 +91,11 @@ struct vie_problem {
   int p3_variant[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // tuned z-pass variant per (precision, mode)
   int* dflag = nullptr;      // device error flag (NaN, bad input)
   double t_precompute = 0;   // wall seconds of the set-up in vie_problem_create
+  // device-resident GMRES: pinned host copies of the per-member Arnoldi state
+  // (one slot per step in flight) and the events that mark each copy complete
+  void* arn_host = nullptr;
+  size_t arn_host_bytes = 0;
+  cudaEvent_t arn_ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace vie {
@@ -155,9 +160,21 @@ inline int smem_optin_bytes() {
   }
   return v;
 }
+// Whether (current device, kernel) has had its attributes set (first call: no),
+// and marking it done; thread-safe (capi.cu).
+bool kernel_configured(const void* kernel);
+void kernel_mark_configured(const void* kernel);
+// The attribute is set once per device and kernel: a driver call at every
+// launch costs microseconds of host time, which small grids (launch-bound
+// solver loops) pay on every apply.
 template <typename K>
-inline cudaError_t allow_smem(K* kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_bytes());
+inline cudaError_t allow_smem(K* kernel, bool max_carveout = false) {
+  if (kernel_configured((const void*)kernel)) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_bytes());
+  if (e == cudaSuccess && max_carveout)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) kernel_mark_configured((const void*)kernel);
+  return e;
 }
 
 inline int cin_of(int mode) { return mode == KM_MAXWELL6 ? 6 : 3; }
