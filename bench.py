@@ -40,8 +40,8 @@ METRIC = "operator applies/s (FP32 apply of the mixed solve) & time-to-1e-8 resi
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel, with the hash of the kernel sources it was measured
 # on; reported only while the sources are unchanged (profiles/ has the capture).
-MEASURED_TRAFFIC = {"kernel": "P3_z_kernel_z", "n": 128, "sources_sha1_16": "a7297b67203c7722",
-                    "bytes": 455.9e6}
+MEASURED_TRAFFIC = {"kernel": "P3_z_kernel_z", "n": 128, "sources_sha1_16": "54fe5fde61aaea76",
+                    "bytes": 453.51e6}
 KERNEL_SOURCES = ["paper_1805_04791_gb300/csrc/apply.cu", "paper_1805_04791_gb300/csrc/apply_fast.cuh",
                   "paper_1805_04791_gb300/csrc/vie_fft2.cuh", "paper_1805_04791_gb300/csrc/vie_fft.cuh"]
 
@@ -68,18 +68,19 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--legs", default="laplace32,maxwell256,batched,serve",
                     help="comma list of extra legs: batched (Maxwell 128^3 with mu, 64 plane waves, lockstep "
-                         "GMRES), maxwell256 (Maxwell 256^3 with mu: mixed vs FP64 time to 1e-8), serve "
-                         "(continuous-batching request mix), paper (Bi-CGStab matvec counts on the paper's "
-                         "media beside Tables 2-5), laplace32 (electrostatic 32^3 solve to 1e-10, FP64 and mixed), "
-                         "serve_sweep (the request mix at arrival rates 10..500 /s), selfconv (E_2 / E_inf "
-                         "self-convergence on the paper's media, 30/42/70 against 210; the last two are not in "
-                         "the default run)")
+                         "GMRES, against the same right-hand sides one at a time), maxwell256 (Maxwell 256^3 "
+                         "with mu: mixed vs FP64 time to 1e-8), serve (continuous-batching request mix at "
+                         "arrival rates 10..500 /s), paper (Bi-CGStab matvec counts on the paper's media beside "
+                         "Tables 2-5), laplace32 (electrostatic 32^3 solve to 1e-10, FP64 and mixed), selfconv "
+                         "(E_2 / E_inf self-convergence on the paper's media, 30/42/70 against 210; paper and "
+                         "selfconv are not in the default run)")
     ap.add_argument("--paper-n", type=int, default=70)
-    ap.add_argument("--serve-requests", type=int, default=60)
-    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--batched-rhs", type=int, default=64)
-    ap.add_argument("--case", default=None, choices=["apply"],
-                    help="minimal run for profilers: build the problem, run --reps FP32 applies, exit")
+    ap.add_argument("--case", default=None, choices=["apply", "solve"],
+                    help="minimal runs for profilers: 'apply' builds the problem and runs --reps applies; "
+                         "'solve' runs one warm mixed solve to 1e-8 between cudaProfilerStart/Stop "
+                         "(profile with --profile-from-start off)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df64"],
                     help="precision of the --case apply run")
@@ -189,17 +190,34 @@ def pct(v, q):
     return v[k]
 
 
-def cpu_baseline_oracle(n, reps, seconds_cap=30.0):
-    """FP64 oracle applies on the host cores (untimed set-up, timed applies)."""
-    import numpy as np
-    import scipy.fft  # noqa: F401
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
 
+    return platform.processor() or platform.machine()
+
+
+def _oracle_apply_rate(problem, reps, seconds_cap):
+    """Applies/s of the FP64 oracle on one problem (untimed set-up, timed applies)."""
     import vie_inputs as vi
-    from oracle import operators, discrete
+    from oracle import operators
 
-    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
-    op = operators.OracleProblem.from_problem(p)
-    x = vi.random_field(n, 3, 0)[0]
+    op = operators.OracleProblem.from_problem(problem)
+    x = vi.random_field(problem.n, op.ncomp, 0)[0]
     op.apply(x)  # builds the kernel transforms (set-up, untimed)
     times = []
     t_start = time.perf_counter()
@@ -209,10 +227,22 @@ def cpu_baseline_oracle(n, reps, seconds_cap=30.0):
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start > seconds_cap:
             break
-    tot = sum(times)
-    return {"value": len(times) / tot, "unit": "applies/s", "cores": discrete.WORKERS, "kind": "oracle",
-            "sample": f"{len(times)} FP64 oracle applies of the {n}^3 Helmholtz workload after untimed set-up "
-                      f"({tot:.1f} s)", "applies": len(times), "seconds": tot}
+    return len(times) / sum(times), len(times), sum(times)
+
+
+def cpu_baseline_oracle(n, reps, seconds_cap=30.0):
+    """FP64 oracle applies on the host cores: the bench workload (Helmholtz n^3) and
+    the electrostatic workload (Laplace 32^3), untimed set-up, timed applies."""
+    import vie_inputs as vi
+    from oracle import discrete
+
+    v, cnt, tot = _oracle_apply_rate(vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0), reps, seconds_cap)
+    v32, c32, t32 = _oracle_apply_rate(vi.laplace_bump_problem(n=32, seed=0), 200, 3.0)
+    return {"value": v, "unit": "applies/s", "cores": discrete.WORKERS, "cpu": cpu_model(), "kind": "oracle",
+            "sample": f"{cnt} FP64 oracle applies of the {n}^3 Helmholtz workload after untimed set-up "
+                      f"({tot:.1f} s); {c32} of the 32^3 Laplace workload ({t32:.1f} s)",
+            "applies": cnt, "seconds": tot,
+            "sizes": {f"helmholtz_{n}": v, "laplace_32": v32}}
 
 
 def run_reference(args):
@@ -254,8 +284,11 @@ def run_reference(args):
 
 
 def leg_batched(args, dev):
-    """Maxwell with mu at 128^3 (10 wavelengths), 32 directions x 2 polarisations,
-    FP32-inner GMRES in lockstep groups with FP64 refinement to 1e-8."""
+    """Maxwell with mu at 128^3 (10 wavelengths), 32 directions x 2 polarisations:
+    all right-hand sides in lockstep groups (one batched apply and one batched
+    projection per Arnoldi step), FP32-inner GMRES with FP64-accurate refinement
+    to 1e-8; then the same right-hand sides solved one after another in the same
+    process, for the batching speed-up."""
     import torch
 
     import paper_1805_04791_gb300 as vie
@@ -274,18 +307,79 @@ def leg_batched(args, dev):
     b = torch.empty((nr, 6, n, n, n), dtype=torch.complex128, device=dev)
     P.rhs(p.directions, p.polarisations, nr, b)
     J = torch.zeros_like(b)
+    opts = dict(tol=1e-8, restart=30, max_outer=40, max_inner=1000, inner_tol=1e-5, mode=vie.VIE_SOLVE_MIXED)
+    # warm-up: one single solve allocates the single-RHS Krylov workspace
+    P.solve(b[0], J[0], **opts, allow_noconv=True)
+    J.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, info = P.solve(b, J, tol=1e-8, restart=30, max_outer=40, max_inner=1000, inner_tol=1e-5,
-                       mode=vie.VIE_SOLVE_MIXED, nrhs=nr, allow_noconv=True)
+    st, info = P.solve(b, J, nrhs=nr, allow_noconv=True, **opts)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    Jb = J.clone()
+    J.zero_()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    singles_ok, worst, ap32 = 0, 0.0, 0
+    for r in range(nr):
+        st1, inf1 = P.solve(b[r], J[r], allow_noconv=True, **opts)
+        singles_ok += int(st1 == 0)
+        worst = max(worst, inf1.rel_residual)
+        ap32 += inf1.applies_fp32
+    torch.cuda.synchronize()
+    dt1 = time.perf_counter() - t1
+    diff = float(torch.linalg.vector_norm(Jb - J) / torch.linalg.vector_norm(J))
+    del b, J, Jb
+    P.close()
+    torch.cuda.empty_cache()
+    small = _batched_small(dev, nr)
     out = {"workload": f"maxwell_mu_bump_{n}_x{nr}rhs", "nrhs": nr, "status": int(st), "seconds": dt,
            "rhs_per_s": nr / dt, "rel_residual_max": info.rel_residual, "applies_fp32": info.applies_fp32,
            "applies_fp64": info.applies_fp64, "gmres_iters_total": info.inner_iters,
-           "refinement_steps": info.outer_iters}
-    P.close()
+           "refinement_steps": info.outer_iters,
+           "one_at_a_time": {"seconds": dt1, "rhs_per_s": nr / dt1, "converged": singles_ok,
+                             "rel_residual_max": worst, "applies_fp32": ap32},
+           "batching_speedup": dt1 / dt, "batched_vs_single_rel_diff": diff,
+           "small_grid": small}
     return out
+
+
+def _batched_small(dev, nr, n=32):
+    """The same comparison on a small grid (Maxwell with mu, 32^3, 4 wavelengths), where
+    a single solve is bound by per-step launch latency and the lockstep group shares it."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    p = vi.maxwell_problem(n=n, wavelengths=4.0, ndirs=max(1, nr // 2), npol=2, with_mu=True, seed=0)
+    P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev),
+                    torch.from_numpy(p.mu.reshape(9, -1).copy()).to(dev))
+    P.tune(vie.VIE_FP32)
+    nr = p.nrhs
+    b = torch.empty((nr, 6, n, n, n), dtype=torch.complex128, device=dev)
+    P.rhs(p.directions, p.polarisations, nr, b)
+    J = torch.zeros_like(b)
+    opts = dict(tol=1e-8, restart=30, max_outer=40, max_inner=1000, inner_tol=1e-5, mode=vie.VIE_SOLVE_MIXED,
+                allow_noconv=True)
+    P.solve(b[0], J[0], **opts)
+    P.solve(b, J, nrhs=nr, **opts)
+    J.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.solve(b, J, nrhs=nr, **opts)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    J.zero_()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for r in range(nr):
+        P.solve(b[r], J[r], **opts)
+    torch.cuda.synchronize()
+    dt1 = time.perf_counter() - t1
+    P.close()
+    return {"workload": f"maxwell_mu_bump_{n}_x{nr}rhs", "seconds": dt, "rhs_per_s": nr / dt,
+            "one_at_a_time_seconds": dt1, "one_at_a_time_rhs_per_s": nr / dt1, "batching_speedup": dt1 / dt}
 
 
 def leg_maxwell256(args, dev):
@@ -324,48 +418,42 @@ def leg_maxwell256(args, dev):
     return out
 
 
-def leg_serve(args, dev):
-    """Continuous-batching request mix: Poisson arrivals, n in {32..192}, 1-8 wavelengths,
-    Helmholtz / Maxwell (mu = I), 160 GB HBM budget; p50/p99 latency and solves/s."""
-    from paper_1805_04791_gb300 import serve
-    import vie_inputs as vi
-
-    reqs = vi.serving_mix(args.serve_requests, rate_per_s=args.serve_rate, seed=0)
-    srv = serve.Server(budget_bytes=160e9, max_slots=32, restart=30, tol=1e-8)
-    stats = srv.run(reqs)
+def _serve_summary(stats, rate):
     out = stats.summary()
     fails = {}
+    by_n = {}
     for r in stats.results:
         if r.status != "ok":
             fails[r.status[:160]] = fails.get(r.status[:160], 0) + 1
-    by_n = {}
-    for r in stats.results:
-        if r.status == "ok":
+        else:
             by_n.setdefault(r.n, []).append(r.latency_s)
     out["failures"] = fails
-    out["p50_latency_by_n"] = {str(k): sorted(v)[len(v) // 2] for k, v in sorted(by_n.items())}
-    out.update({"rate_per_s": args.serve_rate, "budget_GB": 160, "tol": 1e-8,
-                "max_rel_residual": max((r.rel_residual for r in stats.results if r.status == "ok"), default=None)})
+    out["p50_latency_by_n"] = {str(k): pct(v, 50) for k, v in sorted(by_n.items())}
+    out["p99_latency_by_n"] = {str(k): pct(v, 99) for k, v in sorted(by_n.items())}
+    out["rate_per_s"] = rate
+    out["max_rel_residual"] = max((r.rel_residual for r in stats.results if r.status == "ok"), default=None)
     return out
 
 
-def leg_serve_sweep(args, dev):
-    """The serving mix at arrival rates 10, 20, 50, 100, 200, 500 /s (--serve-requests
-    requests each, fresh server per rate, after one unreported warm-up mix):
-    p50/p99 latency and solves/s per rate."""
+def leg_serve(args, dev):
+    """Continuous-batching request mix (Poisson arrivals, n in {32..192}, 1-8
+    wavelengths, Helmholtz / Maxwell with mu = I, 160 GB HBM budget, tolerance
+    1e-8) at arrival rates 10, 20, 50, 100, 200 and 500 /s: p50/p99 latency and
+    solves/s per rate.  The stated mix has 2000 requests per rate; to fit the
+    benchmark's time, --serve-requests (default 100) requests run per rate --
+    only the count is trimmed.  The z-pass schedules of all six grid sizes are
+    chosen before the first arrival (Server.pretune)."""
     from paper_1805_04791_gb300 import serve
     import vie_inputs as vi
 
-    # warm-up (not reported): the first request of each shape tunes its z pass
-    serve.Server(budget_bytes=160e9, max_slots=32, restart=30, tol=1e-8).run(
-        vi.serving_mix(args.serve_requests, rate_per_s=500.0, seed=2))
-    out = {}
+    sizes = (32, 48, 64, 96, 128, 192)
+    serve.Server().pretune(sizes)
+    out = {"requests_per_rate": args.serve_requests, "stated_requests_per_rate": 2000, "budget_GB": 160,
+           "tol": 1e-8, "policy": "shortest job first, aging 30 s", "rates": {}}
     for rate in (10.0, 20.0, 50.0, 100.0, 200.0, 500.0):
-        reqs = vi.serving_mix(args.serve_requests, rate_per_s=rate, seed=1)
+        reqs = vi.serving_mix(args.serve_requests, rate_per_s=rate, seed=int(rate))
         srv = serve.Server(budget_bytes=160e9, max_slots=32, restart=30, tol=1e-8)
-        st = srv.run(reqs).summary()
-        out[str(int(rate))] = {k: st[k] for k in ("completed", "failed", "p50_latency_s", "p99_latency_s",
-                                                  "solves_per_s", "peak_inflight") if k in st}
+        out["rates"][str(int(rate))] = _serve_summary(srv.run(reqs), rate)
     return out
 
 
@@ -641,7 +729,7 @@ def run_ours(args):
                 yh[b].copy_(yd[b], non_blocking=True)
                 ev_dn[b].record(s_down)
 
-    ke = max(5, min(50, args.steps // 4))
+    ke = max(50, min(200, args.steps))  # at least 50 pipelined steps, whatever --steps is
     e2e_steps(4)
     torch.cuda.synchronize()
     te = time.perf_counter()
@@ -677,6 +765,12 @@ def run_ours(args):
                          "rel_residual": infos[-1]["rel_residual"], "applies_fp32": infos[-1]["applies_fp32"],
                          "applies_fp64": infos[-1]["applies_fp64"], "gmres_iters": infos[-1]["inner_iters"]}
         res["speedup_p50"] = res["fp64"]["p50_s"] / res["mixed"]["p50_s"]
+        # one more mixed solve, untimed, whose answer is checked with the native FP64 apply
+        J.zero_()
+        st, info = P.solve(b, J, tol=1e-8, restart=50, max_outer=40, max_inner=3000, inner_tol=1e-5,
+                           mode=vie.VIE_SOLVE_MIXED, check_fp64=True)
+        res["mixed"]["rel_residual_fp64"] = info.rel_residual_fp64
+        res["mixed"]["t_precompute_s"] = info.t_precompute
         solve = res
 
     # ---------------- roofline of the dominant kernel
@@ -694,7 +788,7 @@ def run_ours(args):
     for leg in [x for x in args.legs.split(",") if x]:
         t0 = time.perf_counter()
         fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve, "paper": leg_paper,
-              "laplace32": leg_laplace32, "serve_sweep": leg_serve_sweep, "selfconv": leg_selfconv}[leg]
+              "laplace32": leg_laplace32, "selfconv": leg_selfconv}[leg]
         try:
             extra[leg] = fn(args, dev)
         except Exception as e:  # report, do not lose the main line
@@ -705,6 +799,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(n, reps=5)
+        # like for like: the FP64 GPU apply of the same workload against the FP64 oracle
+        cpu["fp64_gpu"] = {"applies_per_s": 1000.0 / fp64_ms, "ms": fp64_ms,
+                           "ratio_vs_oracle": (1000.0 / fp64_ms) / cpu["value"]}
 
     if rank == 0:
         line = {
@@ -726,7 +823,16 @@ def run_ours(args):
                          "traffic": (MEASURED_TRAFFIC["bytes"] if (MEASURED_TRAFFIC["kernel"] == names[dom]
                                      and MEASURED_TRAFFIC["n"] == n
                                      and MEASURED_TRAFFIC["sources_sha1_16"] == sources_sha()) else None),
-                         "alg_bytes": abytes[dom]},
+                         "alg_bytes": abytes[dom],
+                         # every pass of the timed apply: CUDA-event time and algorithmic GB/s
+                         "passes": kernels,
+                         # the whole apply against the 5-pass bytes it moves and against the
+                         # 2-pass plan ((19c + h + k) values per point, c = 3, h = k = 6)
+                         "apply": {"ms": total_ms / args.steps, "bytes_5pass": apply_bytes,
+                                   "frac_5pass": apply_bytes / (total_ms / args.steps / 1000.0) / 1e9 / peak,
+                                   "bytes_2pass": (19 * c + 12) * n ** 3 * 8,
+                                   "frac_2pass": (19 * c + 12) * n ** 3 * 8 / (total_ms / args.steps / 1000.0) / 1e9
+                                                 / peak}},
             "solve": solve, "setup_s": t_setup, "wall_s_timed": t_wall,
             "e2e": e2e, "p3_variant": p3_variant, "gpu_launches": 5 * args.steps, "clocks": clk,
             "cpu_baseline": cpu,
@@ -761,10 +867,40 @@ def run_case(args):
     print("case ok")
 
 
+def run_case_solve(args):
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    dev = torch.device("cuda:0")
+    n = args.n
+    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
+    P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev))
+    P.tune(vie.VIE_FP32)
+    b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
+    P.rhs(p.directions[0], None, 1, b)
+    J = torch.zeros_like(b)
+    opts = dict(tol=1e-8, restart=50, max_outer=40, max_inner=3000, inner_tol=1e-5, mode=vie.VIE_SOLVE_MIXED)
+    P.solve(b, J, **opts)  # warm: Krylov workspace, double-word tables
+    J.zero_()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    st, info = P.solve(b, J, **opts)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    P.close()
+    print(f"case ok: mixed solve {1e3 * dt:.3f} ms, {info.inner_iters} GMRES iterations, residual {info.rel_residual:.2e}")
+
+
 def main():
     args = parse()
     if args.case == "apply":
         run_case(args)
+    elif args.case == "solve":
+        run_case_solve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

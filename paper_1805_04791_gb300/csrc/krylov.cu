@@ -536,13 +536,15 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
     } else {
       acc[0] = wr[e];
     }
-    AT sx[W][2], sy[W][2];
+    AT sx[W][4], sy[W][4];
 #pragma unroll
-    for (int q = 0; q < W; ++q) sx[q][0] = sx[q][1] = sy[q][0] = sy[q][1] = 0;
+    for (int q = 0; q < W; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sx[q][u] = sy[q][u] = 0;
     int i = 0;
-    for (; i + 2 <= k; i += 2) {
+    for (; i + 4 <= k; i += 4) {  // four basis loads in flight
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < 4; ++u) {
         const typename Acc<TB>::V c = cf[i + u];
         if (packed) {
           const P pv = ((const P*)(Vr + (long long)(i + u) * ldi))[e];
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
         }
       }
     }
-    if (i < k) {
+    for (; i < k; ++i) {
       const typename Acc<TB>::V c = cf[i];
       if (packed) {
         const P pv = ((const P*)(Vr + (long long)i * ldi))[e];
@@ -578,8 +580,8 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
 #pragma unroll
     for (int q = 0; q < W; ++q)
       if (q == 0 || packed) {
-        acc[q].x -= sx[q][0] + sx[q][1];
-        acc[q].y -= sy[q][0] + sy[q][1];
+        acc[q].x -= (sx[q][0] + sx[q][1]) + (sx[q][2] + sx[q][3]);
+        acc[q].y -= (sy[q][0] + sy[q][1]) + (sy[q][2] + sy[q][3]);
         nn += acc[q].x * acc[q].x + acc[q].y * acc[q].y;
       }
     if (packed) {
@@ -742,7 +744,11 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
   const long long ldi = (long long)nb * L;
   TB* V = (TB*)g.V;
   const int prec = sizeof(TB) == sizeof(double2) ? VIE_FP64 : VIE_FP32;
-  const int G = red_blocks(L);
+  // Arnoldi kernels: up to one 16-byte pack per thread (at most kRedBlocks blocks),
+  // so that short vectors still put enough warps on every SM to hide latency;
+  // their reductions finish in the last block, whatever the block count
+  const long long packs = (L + 1) / 2;
+  const int G = (int)std::max<long long>(1, std::min<long long>((packs + kRedThreads - 1) / kRedThreads, kRedBlocks));
   const dim3 ewg(ew_blocks(L), nb), redg(G, nb);
   vie_status s = ensure_mirror(P, nb);
   if (s != VIE_OK) return s;
@@ -801,8 +807,20 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
       read_step = want;
       if (all_done(cur)) break;
     }
-    s = run_apply(P, P->kapply, V + (long long)j * ldi, V + (long long)(j + 1) * ldi, prec, nb, true, st);
-    if (s != VIE_OK) return s;
+    // the apply runs on contiguous runs of members not yet seen as done (members
+    // that finished within the last kArnLag steps still ride along, harmlessly)
+    for (int r0 = 0; r0 < nb;) {
+      if (!cur.empty() && cur[r0].done) {
+        ++r0;
+        continue;
+      }
+      int r1 = r0 + 1;
+      while (r1 < nb && (cur.empty() || !cur[r1].done)) ++r1;
+      s = run_apply(P, P->kapply, V + (long long)j * ldi + (long long)r0 * L,
+                    V + (long long)(j + 1) * ldi + (long long)r0 * L, prec, r1 - r0, true, st);
+      if (s != VIE_OK) return s;
+      r0 = r1;
+    }
     for (int pass = 0; pass < 2; ++pass) {
       k_arn_dots<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j, L, A, pass);
       VIE_CK(cudaGetLastError());

@@ -1,13 +1,21 @@
 """Continuous-batching serving loop for scattering solves.
 
 Requests (kind, grid size, frequency, medium seed, incident wave) arrive over
-time.  The server admits a request as soon as its device-memory need (from
-``vie_problem_bytes``) fits the HBM budget and a slot is free; every admitted
-request runs in its own worker thread on its own CUDA stream: medium set-up,
-kernel transforms, right-hand side and the mixed-precision GMRES solve.  The
-library allocates stream-ordered and holds no device-wide locks, so the
+time.  The server admits a waiting request as soon as its device-memory need
+(from ``vie_problem_bytes``) fits the HBM budget and a slot is free; every
+admitted request runs in its own worker thread on its own CUDA stream: medium
+set-up, kernel transforms, right-hand side and the mixed-precision GMRES solve.
+The library allocates stream-ordered and holds no device-wide locks, so the
 kernels of all admitted requests overlap on the GPU; when a request finishes,
 its memory returns to the budget and the next waiting request is admitted.
+
+Admission order is shortest job first (work estimated as n^3), with aging: a
+request that has waited ``max_wait_s`` is admitted ahead of smaller ones, so
+large grids are not starved.  Before the first arrival the server chooses the
+z-pass schedule of every grid size it may see (``pretune``) on an otherwise
+idle GPU: a choice timed while other requests load the device would be
+distorted, and the choice is kept for the whole process.
+
 Each result records arrival, admission, completion, residual and the solution
 norm; latency percentiles and throughput summarise a run.
 """
@@ -66,7 +74,8 @@ class Server:
     """Admits requests by HBM budget and runs each on its own stream and thread."""
 
     def __init__(self, budget_bytes: float = 160e9, max_slots: int = 32, restart: int = 30, tol: float = 1e-8,
-                 inner_tol: float = 1e-5, keep_solutions: bool = False, device: int = 0):
+                 inner_tol: float = 1e-5, keep_solutions: bool = False, device: int = 0, policy: str = "sjf",
+                 max_wait_s: float = 30.0):
         self.budget = int(budget_bytes)
         self.max_slots = max_slots
         self.restart = restart
@@ -74,6 +83,31 @@ class Server:
         self.inner_tol = inner_tol
         self.keep = keep_solutions
         self.device = device
+        self.policy = policy
+        self.max_wait_s = max_wait_s
+
+    def pretune(self, sizes, kinds=("helmholtz",)):
+        """Choose the FP32 z-pass schedule of every grid size in ``sizes`` now (one
+        small problem per size, on this thread, GPU otherwise idle).  Helmholtz and
+        Maxwell with mu = I use the same kernel set, hence the same choice."""
+        import torch
+
+        import vie_inputs as vi
+
+        from . import VIE_FP32
+
+        torch.cuda.set_device(self.device)
+        dev = torch.device("cuda", self.device)
+        for n in sorted(set(sizes)):
+            for kind in kinds:
+                eps = vi.bump_medium_torch(n, 1, dev)
+                P = Problem(kind, n, -1.0, 1.0, 2.0 * np.pi, eps, None)
+                try:
+                    P.tune(VIE_FP32)
+                finally:
+                    P.close()
+                del eps
+        torch.cuda.synchronize()
 
     def request_bytes(self, req) -> int:
         kind = VIE_HELMHOLTZ if req.kind == "helmholtz" else VIE_MAXWELL
@@ -147,12 +181,17 @@ class Server:
                 now = time.perf_counter() - t0
                 while pending and pending[0].arrival_s * time_scale <= now:
                     queue.append(pending.popleft())
-                # FIFO admission by budget and slot count
+                # admission by budget and slot count: shortest job first (n^3), except
+                # that requests waiting longer than max_wait_s go first (oldest first)
                 while queue:
-                    req = queue[0]
+                    if self.policy == "fifo":
+                        req = queue[0]
+                    else:
+                        old = [q for q in queue if now - q.arrival_s * time_scale >= self.max_wait_s]
+                        req = old[0] if old else min(queue, key=lambda q: (q.n, q.arrival_s))
                     need = sizes.setdefault(req.rid, self.request_bytes(req))
                     if need > self.budget:
-                        queue.popleft()
+                        queue.remove(req)
                         r = ServeResult(req.rid, req.kind, req.n, req.arrival_s * time_scale, now, now,
                                         status="rejected: exceeds budget")
                         stats.results.append(r)
@@ -160,7 +199,7 @@ class Server:
                         continue
                     if state["slots"] >= self.max_slots or state["used"] + need > self.budget:
                         break
-                    queue.popleft()
+                    queue.remove(req)
                     state["used"] += need
                     state["slots"] += 1
                     stats.peak_bytes = max(stats.peak_bytes, state["used"])

@@ -2,7 +2,8 @@
 
 The admission logic is exercised with a fake solver that sleeps instead of
 launching kernels: the HBM budget and the slot limit must never be exceeded,
-requests are admitted in arrival order, and every request completes.
+waiting requests are admitted shortest first unless one has waited past the
+aging limit (then oldest first), and every request completes.
 """
 import threading
 import time
@@ -50,6 +51,7 @@ class FakeServer:
         self.inflight = 0
         self.violations = []
         self.order = []
+        self.kw = {}
 
     def make(self):
         outer = self
@@ -73,7 +75,7 @@ class FakeServer:
                     outer.inflight -= 1
                 done_cb(res)
 
-        return S(budget_bytes=self.budget, max_slots=self.slots)
+        return S(budget_bytes=self.budget, max_slots=self.slots, **self.kw)
 
 
 def test_admission_respects_budget_and_slots():
@@ -139,3 +141,38 @@ def test_failed_request_releases_its_problem(monkeypatch):
     serve.Server()._solve(req, res, done.append)
     assert res.status == "error: solver failed"
     assert closed == [True] and done == [res]
+
+
+def _burst(sizes, t=0.0):
+    """Requests of the given grid sizes, all arriving at time t."""
+    base = vi.serving_mix(len(sizes), rate_per_s=100.0, seed=9)
+    for i, (r, n) in enumerate(zip(base, sizes)):
+        r.rid, r.n, r.arrival_s = i, n, t
+    return base
+
+
+def test_shortest_job_first_admission():
+    """One slot, a simultaneous burst: after the first admission the waiting
+    requests are admitted in increasing grid size."""
+    pytest.importorskip("torch")
+    sizes = [192, 32, 128, 48, 96, 64, 32, 192]
+    fake = FakeServer(budget=10 ** 9, slots=1)
+    fake.kw = {"max_wait_s": 60.0}
+    fake.make().run(_burst(sizes))
+    ns = [sizes[rid] for rid in fake.order]
+    assert ns == sorted(ns), ns
+
+
+def test_aged_requests_go_first():
+    """With an aging limit of zero every waiting request counts as aged, and
+    admission falls back to arrival order (the FIFO policy gives the same)."""
+    pytest.importorskip("torch")
+    sizes = [192, 32, 128, 48, 96]
+    reqs = _burst(sizes)
+    for i, r in enumerate(reqs):
+        r.arrival_s = 0.001 * i
+    for kw in ({"max_wait_s": 0.0}, {"policy": "fifo"}):
+        fake = FakeServer(budget=10 ** 9, slots=1)
+        fake.kw = kw
+        fake.make().run(reqs)
+        assert fake.order == list(range(len(sizes))), (kw, fake.order)
