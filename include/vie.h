@@ -54,6 +54,8 @@
  *                       FP64 apply instead of the double-word one.
  * - VIE_SETUP_FP64=1    the set-up's kernel-transform FFTs run in native FP64
  *                       instead of double-word arithmetic.
+ * - VIE_GRAPHS=0        single right-hand-side GMRES steps are launched kernel by
+ *                       kernel instead of being replayed from captured CUDA graphs.
  */
 #ifndef VIE_H
 #define VIE_H

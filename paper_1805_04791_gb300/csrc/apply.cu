@@ -349,14 +349,9 @@ static vie_status tune_dispatch(vie_problem* P, const KernelSet& K, void* B, int
   }
 }
 
-template <typename T>
-static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                              bool with_identity, cudaStream_t st) {
-  typedef typename CT<T>::V V;
-  const int n = P->n, M = 2 * n;
-  const int cin = cin_of(K.mode), cout = cout_of(K.mode);
-  const int C = std::max(cin, cout);
-  const size_t need = apply_workspace_bytes(n, C, nrhs, Prec<T>::id);
+vie_status ensure_apply_workspace(vie_problem* P, const KernelSet& K, int prec, int nrhs, cudaStream_t st) {
+  const int C = std::max(cin_of(K.mode), cout_of(K.mode));
+  const size_t need = apply_workspace_bytes(P->n, C, nrhs, prec);
   if (P->ws.bytes < need) {
     dfree(P->ws.buf, st);  // stream-ordered: earlier work on st completes first
     P->ws.buf = nullptr;
@@ -368,6 +363,20 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
       return VIE_ENOMEM;
     }
     P->ws.bytes = need;
+  }
+  return VIE_OK;
+}
+
+template <typename T>
+static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
+                              bool with_identity, cudaStream_t st) {
+  typedef typename CT<T>::V V;
+  const int n = P->n, M = 2 * n;
+  const int cin = cin_of(K.mode), cout = cout_of(K.mode);
+  const int C = std::max(cin, cout);
+  {
+    vie_status e = ensure_apply_workspace(P, K, Prec<T>::id, nrhs, st);
+    if (e != VIE_OK) return e;
   }
   V* A = (V*)P->ws.buf;
   V* B = A + (size_t)nrhs * C * n * n * M;

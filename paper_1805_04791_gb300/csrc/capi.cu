@@ -87,6 +87,11 @@ static void free_problem(vie_problem* P) {
   for (cudaEvent_t e : P->arn_ev)
     if (e) cudaEventDestroy(e);
   if (P->arn_host) cudaFreeHost(P->arn_host);
+  for (cudaGraphExec_t g : P->graph_exec)
+    if (g) cudaGraphExecDestroy(g);
+  for (cudaEvent_t e : P->cap_ev)
+    if (e) cudaEventDestroy(e);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   delete P;
 }
 

@@ -448,9 +448,16 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_dots(const TB* __restrict__
   }
 }
 
-// Finalise step j of member r (one thread): Hessenberg column h (i <= j) and
-// h_{j+1,j} = hn; rotations, residual estimate, next scale, done flag.
+// Finalise step j of member r (called by the whole block, thread 0 does the
+// serial part): Hessenberg column h (i <= j) and h_{j+1,j} = hn; rotations,
+// residual estimate, next scale, done flag.  The column and the earlier
+// rotations are staged in shared memory by all threads first, so that the
+// serial rotation chain runs on shared memory instead of making a dependent
+// global-memory round trip per rotation.
+static const int kMaxRestart = 200;
 __device__ void arn_finalize(ArnLayout& A, int r, int j, const double2* h0, const double2* h1, double hn) {
+  __shared__ double2 col[kMaxRestart + 1], csh[kMaxRestart], snh[kMaxRestart];
+  __shared__ int bad;
   const int m = A.m;
   ArnState* S = A.st + r;
   double2* Rc = A.R + ((long long)r * m + j) * (m + 1);
@@ -458,36 +465,46 @@ __device__ void arn_finalize(ArnLayout& A, int r, int j, const double2* h0, cons
   double2* sn = A.sn + (long long)r * m;
   double2* g = A.gv + (long long)r * (m + 1);
   double* sc = A.sc + (long long)r * (m + 2);
-  bool finite = isfinite(hn) && isfinite(S->wn2);
-  for (int i = 0; i <= j; ++i) {
+  if (threadIdx.x == 0) bad = !(isfinite(hn) && isfinite(S->wn2));
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     double2 v = h0[i];
     if (h1) v = v + h1[i];
-    finite = finite && isfinite(v.x) && isfinite(v.y);
-    Rc[i] = v;
+    if (!(isfinite(v.x) && isfinite(v.y))) bad = 1;
+    col[i] = v;
+    if (i < j) {
+      csh[i] = cs[i];
+      snh[i] = sn[i];
+    }
   }
-  if (!finite) {
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (bad) {
     S->nan = 1;
     S->done = 1;
     return;
   }
   // earlier rotations G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]] on rows i, i+1
+  double2 a = col[0];
   for (int i = 0; i < j; ++i) {
-    const double2 a = Rc[i], b = Rc[i + 1];
-    Rc[i] = cmul(dconj(cs[i]), a) + cmul(dconj(sn[i]), b);
-    Rc[i + 1] = cmul(cs[i], b) - cmul(sn[i], a);
+    const double2 b = col[i + 1];
+    col[i] = cmul(dconj(csh[i]), a) + cmul(dconj(snh[i]), b);
+    a = cmul(csh[i], b) - cmul(snh[i], a);
   }
-  const double2 a = Rc[j];
   const double den = sqrt(dnorm2(a) + hn * hn);
-  const double2 c = den > 0 ? dscale(1.0 / den, a) : make_double2(1, 0);
-  const double2 sv = den > 0 ? make_double2(hn / den, 0) : make_double2(0, 0);
+  const double id = den > 0 ? 1.0 / den : 0.0;
+  const double2 c = den > 0 ? dscale(id, a) : make_double2(1, 0);
+  const double2 sv = make_double2(hn * id, 0);
+  col[j] = cmul(dconj(c), a) + dscale(hn, dconj(sv));
+  for (int i = 0; i <= j; ++i) Rc[i] = col[i];
   cs[j] = c;
   sn[j] = sv;
-  Rc[j] = cmul(dconj(c), a) + dscale(hn, dconj(sv));
   const double2 gj = g[j];
-  g[j + 1] = dscale(-1.0, cmul(sv, gj));
+  const double2 gn = dscale(-1.0, cmul(sv, gj));
+  g[j + 1] = gn;
   g[j] = cmul(dconj(c), gj);
   S->steps = j + 1;
-  S->gabs = sqrt(dnorm2(g[j + 1]));
+  S->gabs = sqrt(dnorm2(gn));
   S->reorth = 0;
   if (S->gabs <= S->stop || hn == 0.0) {
     S->done = 1;
@@ -602,6 +619,8 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
     A.partial[((long long)r * ldp + m + 2) * G + blockIdx.x] = make_double2(t, 0.0);
   }
   if (!arn_last_block(A.cnt + r)) return;
+  __shared__ double nw2s;
+  __shared__ int fin;
   if (threadIdx.x < 32) {
     double t = 0;
     for (int b = threadIdx.x; b < G; b += 32) t += __ldcg(&A.partial[((long long)r * ldp + m + 2) * G + b]).x;
@@ -609,13 +628,18 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
     if (threadIdx.x == 0) {
       A.cnt[r] = 0;
       const double nw2 = nonneg(sc[j] * sc[j] * t);  // |w'|^2 at true scale
-      const double2* h0 = A.hcol + (long long)r * 2 * (m + 2);
+      nw2s = nw2;
+      fin = 1;
       if (pass == 0 && nw2 < 0.0625 * S->wn2) {
         S->reorth = 1;  // the second pass finalises
-      } else {
-        arn_finalize(A, r, j, h0, pass == 1 ? h0 + (m + 2) : nullptr, sqrt(nw2));
+        fin = 0;
       }
     }
+  }
+  __syncthreads();
+  if (fin) {
+    const double2* h0 = A.hcol + (long long)r * 2 * (m + 2);
+    arn_finalize(A, r, j, h0, pass == 1 ? h0 + (m + 2) : nullptr, sqrt(nw2s));
   }
 }
 
@@ -716,6 +740,12 @@ static vie_status norms_host(const double2* v, Group& g, std::vector<double>& ou
   return VIE_OK;
 }
 
+// CUDA graphs for single right-hand-side GMRES steps (VIE_GRAPHS=0 turns them off).
+static bool graphs_enabled() {
+  const char* e = getenv("VIE_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
 // Pinned host mirror of the group's per-member state, one slot per step in flight.
 static vie_status ensure_mirror(vie_problem* P, int nb) {
   const size_t need = sizeof(ArnState) * (size_t)nb * kArnSlots;
@@ -795,6 +825,70 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
     }
     return false;
   };
+  // One step: the apply (on contiguous runs of members not yet seen as done when
+  // `compact`; members that finished within the last kArnLag steps still ride
+  // along, harmlessly), both Gram-Schmidt passes, and the state copy + event.
+  auto enqueue_step = [&](int j, cudaStream_t ss, bool compact, bool capturing) -> vie_status {
+    for (int r0 = 0; r0 < nb;) {
+      if (compact && !cur.empty() && cur[r0].done) {
+        ++r0;
+        continue;
+      }
+      int r1 = r0 + 1;
+      while (r1 < nb && !(compact && !cur.empty() && cur[r1].done)) ++r1;
+      vie_status e = run_apply(P, P->kapply, V + (long long)j * ldi + (long long)r0 * L,
+                               V + (long long)(j + 1) * ldi + (long long)r0 * L, prec, r1 - r0, true, ss);
+      if (e != VIE_OK) return e;
+      r0 = r1;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      k_arn_dots<TB><<<redg, kRedThreads, 0, ss>>>(V, ldi, j, L, A, pass);
+      VIE_CK(cudaGetLastError());
+      k_arn_axpy<TB><<<redg, kRedThreads, 0, ss>>>(V, ldi, j, L, A, pass);
+      VIE_CK(cudaGetLastError());
+    }
+    VIE_CK(cudaMemcpyAsync(mirror + (size_t)(j % kArnSlots) * nb, A.st, sizeof(ArnState) * nb,
+                           cudaMemcpyDeviceToHost, ss));
+    // inside a stream capture the record must be External to become an event-record
+    // node of the graph (a plain one only expresses a dependency within the capture)
+    if (capturing) VIE_CK(cudaEventRecordWithFlags(P->arn_ev[j % kArnSlots], ss, cudaEventRecordExternal));
+    else VIE_CK(cudaEventRecord(P->arn_ev[j % kArnSlots], ss));
+    return VIE_OK;
+  };
+  // Single right-hand sides replay each step as a CUDA graph (one per step index,
+  // captured the first time it is needed from the second cycle with the same
+  // layout on), which removes the per-kernel launch costs that dominate small
+  // grids.  Everything a graph bakes in is part of the key.
+  bool use_graphs = false;
+  if (nb == 1 && !P->prof.on && graphs_enabled() && p3_schedule_ready(P, P->kapply, prec)) {
+    s = ensure_apply_workspace(P, P->kapply, prec, nb, st);
+    if (s != VIE_OK) return s;
+    const std::vector<long long> key = {prec, nb, m, G, L, (long long)(uintptr_t)V, (long long)(uintptr_t)A.st,
+                                        (long long)(uintptr_t)A.partial, (long long)(uintptr_t)mirror,
+                                        (long long)(uintptr_t)P->ws.buf, (long long)P->ws.bytes,
+                                        P->p3_variant[prec][P->kapply.mode]};
+    if (key != P->graph_key) {
+      for (cudaGraphExec_t ge : P->graph_exec)
+        if (ge) cudaGraphExecDestroy(ge);
+      P->graph_exec.clear();
+      P->graph_key = key;
+      P->graph_cycles = 0;
+    }
+    if (P->graph_cycles >= 1) {
+      if (!P->cap_stream) VIE_CK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : P->cap_ev)
+        if (!e) VIE_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      use_graphs = true;
+    }
+    ++P->graph_cycles;
+  }
+  cudaStream_t ss = st;
+  if (use_graphs) {  // the steps run on the capture stream, after everything enqueued on st
+    ss = P->cap_stream;
+    VIE_CK(cudaEventRecord(P->cap_ev[0], st));
+    VIE_CK(cudaStreamWaitEvent(ss, P->cap_ev[0], 0));
+    if ((int)P->graph_exec.size() < m) P->graph_exec.resize(m, nullptr);
+  }
   int read_step = -1;
   for (int j = 0; j < m; ++j) {
     // read back the state of step j - kArnLag, or of step j - 1 near convergence
@@ -807,29 +901,33 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
       read_step = want;
       if (all_done(cur)) break;
     }
-    // the apply runs on contiguous runs of members not yet seen as done (members
-    // that finished within the last kArnLag steps still ride along, harmlessly)
-    for (int r0 = 0; r0 < nb;) {
-      if (!cur.empty() && cur[r0].done) {
-        ++r0;
-        continue;
-      }
-      int r1 = r0 + 1;
-      while (r1 < nb && (cur.empty() || !cur[r1].done)) ++r1;
-      s = run_apply(P, P->kapply, V + (long long)j * ldi + (long long)r0 * L,
-                    V + (long long)(j + 1) * ldi + (long long)r0 * L, prec, r1 - r0, true, st);
+    if (!use_graphs) {
+      s = enqueue_step(j, ss, true, false);
       if (s != VIE_OK) return s;
-      r0 = r1;
+      continue;
     }
-    for (int pass = 0; pass < 2; ++pass) {
-      k_arn_dots<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j, L, A, pass);
-      VIE_CK(cudaGetLastError());
-      k_arn_axpy<TB><<<redg, kRedThreads, 0, st>>>(V, ldi, j, L, A, pass);
-      VIE_CK(cudaGetLastError());
+    if (!P->graph_exec[j]) {
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(ss, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const vie_status es = enqueue_step(j, ss, false, true);
+        const cudaError_t ee = cudaStreamEndCapture(ss, &graph);
+        cudaGraphExec_t ge = nullptr;
+        if (es == VIE_OK && ee == cudaSuccess && graph && cudaGraphInstantiate(&ge, graph, 0) == cudaSuccess)
+          P->graph_exec[j] = ge;
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();  // a failed capture leaves the step to direct launches
     }
-    VIE_CK(cudaMemcpyAsync(mirror + (size_t)(j % kArnSlots) * nb, A.st, sizeof(ArnState) * nb,
-                           cudaMemcpyDeviceToHost, st));
-    VIE_CK(cudaEventRecord(P->arn_ev[j % kArnSlots], st));
+    if (P->graph_exec[j]) {
+      VIE_CK(cudaGraphLaunch(P->graph_exec[j], ss));
+    } else {
+      s = enqueue_step(j, ss, false, false);
+      if (s != VIE_OK) return s;
+    }
+  }
+  if (use_graphs) {
+    VIE_CK(cudaEventRecord(P->cap_ev[1], ss));
+    VIE_CK(cudaStreamWaitEvent(st, P->cap_ev[1], 0));
   }
   // back substitution and x += V y on the device; the final state to the host
   k_arn_solve<<<(nb + 63) / 64, 64, 0, st>>>(A, nb);

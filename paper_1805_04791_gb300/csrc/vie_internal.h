@@ -96,6 +96,13 @@ struct vie_problem {
   void* arn_host = nullptr;
   size_t arn_host_bytes = 0;
   cudaEvent_t arn_ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // single right-hand-side GMRES steps replayed as CUDA graphs (one per step
+  // index), valid while every pointer and size baked into them is unchanged
+  cudaStream_t cap_stream = nullptr;  // non-blocking stream the graphs are captured on and run on
+  cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+  std::vector<long long> graph_key;
+  std::vector<cudaGraphExec_t> graph_exec;
+  int graph_cycles = 0;  // cycles run with graph_key (graphs are built from the second on)
 };
 
 namespace vie {
@@ -132,6 +139,9 @@ vie_status build_df(vie_problem* P, cudaStream_t st);
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
                      bool with_identity, cudaStream_t st);
 size_t apply_workspace_bytes(int n, int c, int nrhs, int prec);
+// Grow the padded-intermediate workspace for an apply of K at this precision and
+// nrhs (stream-ordered on st); afterwards run_apply does not allocate.
+vie_status ensure_apply_workspace(vie_problem* P, const KernelSet& K, int prec, int nrhs, cudaStream_t st);
 // Pick (by timing, unless VIE_TUNE=0) the z-pass variant for (prec, K.mode); returns it in *variant.
 vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant, cudaStream_t st);
 // Whether run_apply at this precision can start without choosing a z-pass
