@@ -72,8 +72,10 @@ def parse():
                          "with mu: mixed vs FP64 time to 1e-8), serve (continuous-batching request mix at "
                          "arrival rates 10..500 /s), paper (Bi-CGStab matvec counts on the paper's media beside "
                          "Tables 2-5), laplace32 (electrostatic 32^3 solve to 1e-10, FP64 and mixed), selfconv "
-                         "(E_2 / E_inf self-convergence on the paper's media, 30/42/70 against 210; paper and "
-                         "selfconv are not in the default run)")
+                         "(E_2 / E_inf self-convergence on the paper's media, 30/42/70 against 210), maxwell326 "
+                         "(the first experiment of Sec. 5.2 at 326^3: reduced Maxwell, oscillatory eps, w = 408, "
+                         "Bluestein transforms; set-up, FP32 apply and mixed solve to 1e-8); paper, selfconv and "
+                         "maxwell326 are not in the default run")
     ap.add_argument("--paper-n", type=int, default=70)
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--batched-rhs", type=int, default=64)
@@ -414,6 +416,55 @@ def leg_maxwell256(args, dev):
                      "applies_fp32": info.applies_fp32, "applies_fp64": info.applies_fp64,
                      "gmres_iters": info.inner_iters}
     out["speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    P.close()
+    return out
+
+
+def leg_maxwell326(args, dev):
+    """The first experiment of Sec. 5.2 at its coarse grid: reduced Maxwell (mu = I)
+    at 326^3 on [0,1]^3, eps = (1 + W (1 + 0.1 sin(w x) sin(w y) sin(w z))) I with
+    w = 408, E^in = (0, 0, exp(i w x)).  2n = 652 = 4 x 163 and 3n = 978 = 6 x 163:
+    every transform runs Bluestein's algorithm (padded lengths 1320 and 1960).
+    Set-up time, FP32 apply time, and a mixed solve to 1e-8."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    n, w = 326, 408.0
+    eps = vi.oscillatory_eps_torch(n, dev, w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P = vie.Problem("maxwell", n, 0.0, 1.0, w, eps, None)
+    t_setup = time.perf_counter() - t0
+    del eps
+    torch.cuda.empty_cache()
+    b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
+    P.rhs(np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0]), 1, b)
+    out = {"workload": f"maxwell_oscillatory_{n}", "omega": w, "setup_s": t_setup,
+           "padded_lengths": {"2n": 1320, "3n": 1960}}
+    x32 = b.to(torch.complex64)
+    y32 = torch.empty_like(x32)
+    P.apply(x32, y32, vie.VIE_FP32)
+    torch.cuda.synchronize()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        P.apply(x32, y32, vie.VIE_FP32)
+    e1.record()
+    torch.cuda.synchronize()
+    out["apply_fp32_ms"] = e0.elapsed_time(e1) / reps
+    del x32, y32
+    J = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, info = P.solve(b, J, tol=1e-8, restart=50, max_outer=40, max_inner=600, inner_tol=1e-5,
+                       mode=vie.VIE_SOLVE_MIXED, allow_noconv=True)
+    torch.cuda.synchronize()
+    out["mixed"] = {"seconds": time.perf_counter() - t0, "status": int(st), "rel_residual": info.rel_residual,
+                    "applies_fp32": info.applies_fp32, "applies_fp64": info.applies_fp64,
+                    "gmres_iters": info.inner_iters}
     P.close()
     return out
 
@@ -787,7 +838,8 @@ def run_ours(args):
     extra = {}
     for leg in [x for x in args.legs.split(",") if x]:
         t0 = time.perf_counter()
-        fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "serve": leg_serve, "paper": leg_paper,
+        fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "maxwell326": leg_maxwell326, "serve": leg_serve,
+              "paper": leg_paper,
               "laplace32": leg_laplace32, "selfconv": leg_selfconv}[leg]
         try:
             extra[leg] = fn(args, dev)

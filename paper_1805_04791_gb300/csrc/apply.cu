@@ -4,9 +4,9 @@
 //
 // Five passes over HBM.  For 2n in {64, 96, 128, 192, 256, 384, 512} they are the
 // register-resident kernels of apply_fast.cuh (chosen here, with the z-pass
-// autotuner); every other 2n = 2^a 3^b 5^c 7^d 11^e, and the double-word passes
-// without a fast kernel, run the shared-memory Stockham kernels of this file
-// (vie_fft.cuh):
+// autotuner); every other 2n, and the double-word passes without a fast
+// kernel, run the shared-memory Stockham kernels of this file (vie_fft.cuh,
+// with Bluestein's algorithm when 2n has a prime factor above 11):
 //   P1  x-lines: zero-pad n -> 2n, forward FFT          x [c][n][n][n]    -> A [c][n][n][2n]
 //   P2  y-lines: zero-pad, forward FFT                   A                 -> B [c][n][2n][2n]
 //   P3  z-pencils of all components: zero-pad, forward FFT, per-k kernel
@@ -27,19 +27,21 @@
 #include "apply_fast.cuh"
 
 namespace vie {
-// Generic kernels (any 2n = 2^a 3^b 5^c 7^d 11^e): shared-memory Stockham passes with the
-// twiddle table staged in shared memory (vie_fft.cuh).
+// Generic kernels (any 2n): shared-memory Stockham passes with the twiddle
+// table staged in shared memory, and Bluestein's algorithm on top of them when
+// 2n has a prime factor above 11 (line_fft, vie_fft.cuh).  Tile lines have
+// the plan's inner length Q (= 2n for smooth sizes) plus one.
 // ---------------------------------------------------------------- P1
 template <typename T>
 __global__ void k_p1(const typename IOT<T>::E* __restrict__ x, typename CT<T>::V* __restrict__ A, int n, FftPlan pl,
                      const typename CT<T>::V* __restrict__ twg, int nl, int C) {
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int M = pl.M, LS = M + 1;
+  const int M = pl.M, Q = pl.Q, LS = Q + 1;
   V* tw = (V*)smraw;
-  V* b0 = tw + M;
+  V* b0 = tw + Q;
   V* b1 = b0 + nl * LS;
-  load_tw(tw, twg, M);
+  load_tw(tw, twg, Q);
   const long long N = (long long)n * n * n;
   const int c = blockIdx.y, b = blockIdx.z, nc = gridDim.y;
   const typename IOT<T>::E* src = x + ((long long)b * nc + c) * N;
@@ -52,7 +54,7 @@ __global__ void k_p1(const typename IOT<T>::E* __restrict__ x, typename CT<T>::V
       b0[l * LS + j] = (j < n && r < rows) ? to_v<T>(src[(long long)r * n + j]) : CT<T>::make(0, 0);
   }
   __syncthreads();
-  V* res = tile_fft<-1, T>(b0, b1, pl, tw, nl, LS);
+  V* res = line_fft<-1, T>(b0, b1, pl, tw, twg + Q, nl, LS);
   for (int l = threadIdx.y; l < nl; l += blockDim.y) {
     const int r = r0 + l;
     if (r >= rows) continue;
@@ -68,11 +70,11 @@ __global__ void k_py(const typename CT<T>::V* __restrict__ in, typename CT<T>::V
                      FftPlan pl, const typename CT<T>::V* __restrict__ twg, int nl, int C, int ncomp) {
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int M = pl.M, LS = M + 1;
+  const int M = pl.M, Q = pl.Q, LS = Q + 1;
   V* tw = (V*)smraw;
-  V* b0 = tw + M;
+  V* b0 = tw + Q;
   V* b1 = b0 + nl * LS;
-  load_tw(tw, twg, M);
+  load_tw(tw, twg, Q);
   const int kx0 = blockIdx.x * nl, z = blockIdx.y;
   const int bc = blockIdx.z;  // rhs * ncomp + comp
   const int b = bc / ncomp, c = bc - b * ncomp;
@@ -87,7 +89,7 @@ __global__ void k_py(const typename CT<T>::V* __restrict__ in, typename CT<T>::V
     b0[l * LS + j] = (j < nin) ? src[(long long)j * M + kx0 + l] : CT<T>::make(0, 0);
   }
   __syncthreads();
-  V* res = tile_fft<S, T>(b0, b1, pl, tw, nl, LS);
+  V* res = line_fft<S, T>(b0, b1, pl, tw, twg + Q, nl, LS);
   for (int idx = tid; idx < nl * nout; idx += nt) {
     const int j = idx / nl, l = idx - j * nl;
     dst[(long long)j * M + kx0 + l] = res[l * LS + j];
@@ -113,14 +115,14 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
                      int nl, int C, const typename CT<T>::V* __restrict__ K, int mode) {
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int M = pl.M, LS = M + 1;
+  const int M = pl.M, Q = pl.Q, LS = Q + 1;
   const int cin = (mode == KM_MAXWELL6) ? 6 : 3;
   const int cout = (mode == KM_SYM3) ? 3 : (mode == KM_DIV ? 1 : 6);
   const int cmax = cin > cout ? cin : cout;
   V* tw = (V*)smraw;
-  V* b0 = tw + M;
+  V* b0 = tw + Q;
   V* b1 = b0 + cmax * nl * LS;
-  load_tw(tw, twg, M);
+  load_tw(tw, twg, Q);
   const int kx0 = blockIdx.x * nl, ky = blockIdx.y, b = blockIdx.z;
   const long long zs = (long long)M * M;           // z stride within a component
   const long long cs = (long long)n * zs;          // component stride
@@ -134,7 +136,7 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
     b0[(c * nl + l) * LS + z] = (z < n) ? base[c * cs + z * zs + l] : CT<T>::make(0, 0);
   }
   __syncthreads();
-  V* fw = tile_fft<-1, T>(b0, b1, pl, tw, cin * nl, LS);
+  V* fw = line_fft<-1, T>(b0, b1, pl, tw, twg + Q, cin * nl, LS);
   V* ob = (fw == b0) ? b1 : b0;
   // per-k mixing
   const int O = n + 1;
@@ -182,7 +184,7 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
     for (int c = 0; c < cout; ++c) ob[(c * nl + l) * LS + kz] = o[c];
   }
   __syncthreads();
-  V* iv = tile_fft<+1, T>(ob, fw, pl, tw, cout * nl, LS);
+  V* iv = line_fft<+1, T>(ob, fw, pl, tw, twg + Q, cout * nl, LS);
   for (int idx = tid; idx < cout * nl * n; idx += nt) {
     const int l = idx % nl;
     const int t = idx / nl;
@@ -199,11 +201,11 @@ __global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename IOT
                      const typename CT<T>::V* __restrict__ Hm, int with_identity) {
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int M = pl.M, LS = M + 1;
+  const int M = pl.M, Q = pl.Q, LS = Q + 1;
   V* tw = (V*)smraw;
-  V* b0 = tw + M;
+  V* b0 = tw + Q;
   V* b1 = b0 + cout * nr * LS;
-  load_tw(tw, twg, M);
+  load_tw(tw, twg, Q);
   const int r0 = blockIdx.x * nr, b = blockIdx.y;
   const int rows = n * n;
   const long long N = (long long)n * n * n;
@@ -215,7 +217,7 @@ __global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename IOT
       b0[line * LS + j] = (r < rows) ? src[c * cs + (long long)r * M + j] : CT<T>::make(0, 0);
   }
   __syncthreads();
-  V* res = tile_fft<+1, T>(b0, b1, pl, tw, cout * nr, LS);
+  V* res = line_fft<+1, T>(b0, b1, pl, tw, twg + Q, cout * nr, LS);
   const int tid = flat_tid(), nt = flat_nthreads();
   for (int idx = tid; idx < nr * n; idx += nt) {
     const int r = idx / n, xx = idx - r * n;
@@ -249,25 +251,44 @@ static int pow2_divisor(int M, int target) {
   return nl;
 }
 
-static dim3 line_block(int M) {
+// Threads per tile line: one per 16 elements of the length-Q transform, a power
+// of two up to 128 (32 for every Q <= 512; the long Bluestein lines take more,
+// since only one or two of them fit in a tile).
+static dim3 line_block(const FftPlan& pl) {
   int tx = 1;
-  while (tx * 16 < M && tx < 32) tx <<= 1;
+  while (tx * 16 < pl.Q && tx < 128) tx <<= 1;
   return dim3(tx, 256 / tx);
+}
+
+// Shared memory of a generic pass over `lines` tile lines: staged twiddles and
+// two ping-pong buffers.
+static size_t tile_smem(const FftPlan& pl, size_t vs, int lines) {
+  return vs * ((size_t)pl.Q + 2 * (size_t)lines * (pl.Q + 1));
 }
 
 // Lines per CTA of a one-component generic pass: as many as a 256-thread block
 // holds (one thread row per line), with the tile kept near 72 KB of shared
 // memory so that three CTAs share an SM also for 16-byte elements.
-static int lines_for(int M, size_t vs) {
-  const int cap = 256 / (int)line_block(M).x;
-  int nl = pow2_divisor(M, cap);
-  while (nl > 1 && vs * (M + 2 * (size_t)nl * (M + 1)) > 72 * 1024) nl >>= 1;
+static int lines_for(const FftPlan& pl, size_t vs) {
+  const int cap = 256 / (int)line_block(pl).x;
+  int nl = pow2_divisor(pl.M, cap);
+  while (nl > 1 && tile_smem(pl, vs, nl) > 72 * 1024) nl >>= 1;
   return nl;
 }
 // Block of a generic pass over `lines` lines: no thread row left idle.
-static dim3 block_for(int M, int lines) {
-  const dim3 b = line_block(M);
+static dim3 block_for(const FftPlan& pl, int lines) {
+  const dim3 b = line_block(pl);
   return dim3(b.x, std::max(1, std::min((int)b.y, lines)));
+}
+
+// The generic passes need C tile lines in shared memory at the least (the z
+// pass holds every component of a pencil); long Bluestein lines with six
+// components at 16 bytes per element do not fit and the apply is refused
+// before anything is launched.
+static vie_status check_tiles(const FftPlan& pl, size_t vs, int C) {
+  if (tile_smem(pl, vs, C) <= (size_t)smem_optin_bytes()) return VIE_OK;
+  set_error("grid too large for the generic kernels at this precision and component count (shared memory)");
+  return VIE_EINVAL;
 }
 
 size_t apply_workspace_bytes(int n, int c, int nrhs, int prec) {
@@ -384,6 +405,10 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   const V* Kp = Prec<T>::K(K);
   const FftPlan& pl = P->plan2n;
   const size_t vs = sizeof(V);
+  {
+    vie_status e = check_tiles(pl, vs, C);
+    if (e != VIE_OK) return e;
+  }
   Profiler& pf = P->prof;
   const bool rec = pf.on && pf.count < pf.cap;
   cudaEvent_t* ev = rec ? &pf.ev[(size_t)pf.count * (kProfSlots + 1)] : nullptr;
@@ -431,16 +456,16 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     if (e != VIE_OK) return e;
     if (rec) VIE_CK(cudaEventRecord(ev[1], st));
   } else {
-    const int nl = lines_for(M, vs);
-    const size_t smem = vs * (M + 2 * nl * (M + 1));
+    const int nl = lines_for(pl, vs);
+    const size_t smem = tile_smem(pl, vs, nl);
     VIE_CK(allow_smem(k_p1<T>));
     dim3 grid((n * n + nl - 1) / nl, cin, nrhs);
-    k_p1<T><<<grid, block_for(M, nl), smem, st>>>((const typename IOT<T>::E*)in, A, n, pl, tw, nl, C);
+    k_p1<T><<<grid, block_for(pl, nl), smem, st>>>((const typename IOT<T>::E*)in, A, n, pl, tw, nl, C);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[1], st));
   }
-  const int nly = lines_for(M, vs);
-  const size_t smem_y = vs * (M + 2 * nly * (M + 1));
+  const int nly = lines_for(pl, vs);
+  const size_t smem_y = tile_smem(pl, vs, nly);
   // P2
   if (fs.py) {
     vie_status e = fast_dispatch(2, P, K, in, out, nrhs, with_identity, A, B, C, Prec<T>::id, st);
@@ -449,7 +474,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   } else {
     VIE_CK(allow_smem(k_py<T, -1>));
     dim3 grid(M / nly, n, nrhs * cin);
-    k_py<T, -1><<<grid, block_for(M, nly), smem_y, st>>>(A, B, n, pl, tw, nly, C, cin);
+    k_py<T, -1><<<grid, block_for(pl, nly), smem_y, st>>>(A, B, n, pl, tw, nly, C, cin);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[2], st));
   }
@@ -464,11 +489,11 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   if (!fs.p3) {
     int nl = pow2_divisor(M, 8);
     // two CTAs per SM: the z pass is compute bound and needs the warps
-    while (nl > 1 && vs * (M + 2 * C * nl * (M + 1)) > 110 * 1024) nl >>= 1;
-    const size_t smem = vs * (M + 2 * C * nl * (M + 1));
+    while (nl > 1 && tile_smem(pl, vs, C * nl) > 110 * 1024) nl >>= 1;
+    const size_t smem = tile_smem(pl, vs, C * nl);
     VIE_CK(allow_smem(k_p3<T>));
     dim3 grid(M / nl, M, nrhs);
-    k_p3<T><<<grid, block_for(M, C * nl), smem, st>>>(B, n, pl, tw, nl, C, Kp, K.mode);
+    k_p3<T><<<grid, block_for(pl, C * nl), smem, st>>>(B, n, pl, tw, nl, C, Kp, K.mode);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[3], st));
   }
@@ -480,7 +505,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   } else {
     VIE_CK(allow_smem(k_py<T, +1>));
     dim3 grid(M / nly, n, nrhs * cout);
-    k_py<T, +1><<<grid, block_for(M, nly), smem_y, st>>>(B, A, n, pl, tw, nly, C, cout);
+    k_py<T, +1><<<grid, block_for(pl, nly), smem_y, st>>>(B, A, n, pl, tw, nly, C, cout);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[4], st));
   }
@@ -491,13 +516,13 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     if (rec) VIE_CK(cudaEventRecord(ev[5], st));
   } else {
     int nr = 4;
-    while (nr > 1 && vs * (M + 2 * cout * nr * (M + 1)) > 200 * 1024) nr >>= 1;
-    const size_t smem = vs * (M + 2 * cout * nr * (M + 1));
+    while (nr > 1 && tile_smem(pl, vs, cout * nr) > 200 * 1024) nr >>= 1;
+    const size_t smem = tile_smem(pl, vs, cout * nr);
     VIE_CK(allow_smem(k_p5<T>));
     dim3 grid((n * n + nr - 1) / nr, nrhs);
     const V* He = Prec<T>::He(P);
     const V* Hm = P->has_mu ? Prec<T>::Hm(P) : nullptr;
-    k_p5<T><<<grid, block_for(M, cout * nr), smem, st>>>(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, pl, tw, nr, C,
+    k_p5<T><<<grid, block_for(pl, cout * nr), smem, st>>>(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, pl, tw, nr, C,
                                      cout, He, Hm,
                                      with_identity ? 1 : 0);
     VIE_CK(cudaGetLastError());

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_dots(const TB* __restrict__
   if (threadIdx.x == 0) A.cnt[r] = 0;
   const double* sc = A.sc + (long long)r * (m + 2);
   double2* h = A.hcol + ((long long)r * 2 + pass) * (m + 2);
-  const double sj = sc[j];
+  const double sj = sc[j + 1];  // scale of W_{j+1} as currently stored
   for (int i = threadIdx.x; i < ktot; i += blockDim.x) {
     const double2 raw = A.partial[((long long)r * ldp + i) * G];
     if (i < k) h[i] = dscale(sc[i] * sj, raw);
@@ -509,12 +509,20 @@ __device__ void arn_finalize(ArnLayout& A, int r, int j, const double2* h0, cons
   if (S->gabs <= S->stop || hn == 0.0) {
     S->done = 1;
   } else {
-    sc[j + 1] = sc[j] / hn;
+    sc[j + 1] /= hn;
+    if (j + 1 < m) sc[j + 2] = sc[j + 1];  // W_{j+2} = A W_{j+1} starts at the scale of W_{j+1}
   }
 }
 
-// Pass p: W_{j+1} -= sum_{i <= j} (h_i s_i / s_j) W_i and block partials of |W_{j+1}|^2;
-// the last block decides on the second pass (pass 0) or finalises the step.
+// Pass p: W_{j+1} -= sum_{i <= j} (h_i s_i / s_{j+1}) W_i and block partials of
+// |W_{j+1}|^2; the last block decides on the second pass (pass 0) or finalises
+// the step.  s_{j+1} is the scale W_{j+1} is stored at (v = s W at unit norm).
+// Pass 0 also multiplies W_{j+1} by the power of two c that brings its stored
+// norm into [1/2, 1) before the projection (known from the pass-0 dots), and
+// divides s_{j+1} by c: a power of two leaves every mantissa as it was, and the
+// stored basis stays near unit norm.  Without it each stored vector would be
+// about h_{j+1,j} times the previous one, which overflows the FP32 basis within
+// a cycle when the operator norm is large (tens, at high frequency).
 template <typename TB>
 __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, long long ldi, int j, long long L,
                                                           ArnLayout A, int pass) {
@@ -524,14 +532,24 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
   const int r = blockIdx.y, G = gridDim.x, m = A.m, ldp = m + 3;
   ArnState* S = A.st + r;
   if (S->done || (pass == 1 && !S->reorth)) return;  // block-uniform
-  const double* sc = A.sc + (long long)r * (m + 2);
+  double* sc = A.sc + (long long)r * (m + 2);
   const double2* h = A.hcol + ((long long)r * 2 + pass) * (m + 2);
   const int k = j + 1;
+  const double u = sc[j + 1];
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double f = sc[i] / sc[j];
+    const double f = sc[i] / u;
     cf[i].x = (AT)(h[i].x * f);
     cf[i].y = (AT)(h[i].y * f);
   }
+  // c = 2^-E with |W_{j+1}| = f 2^E, f in [1/2, 1) (|W_{j+1}|^2 = wn2 / u^2), E clamped
+  // so that c stays a normal FP32 number
+  int E = 0;
+  if (pass == 0) {
+    const double rawn = sqrt(S->wn2) / u;
+    if (rawn > 0.0 && isfinite(rawn)) frexp(rawn, &E);
+    E = E < -100 ? -100 : (E > 100 ? 100 : E);
+  }
+  const AT cscale = (AT)ldexp(1.0, -E);
   __syncthreads();
   const TB* Vr = V + (long long)r * L;
   TB* wr = V + (long long)(j + 1) * ldi + (long long)r * L;
@@ -599,6 +617,10 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
       if (q == 0 || packed) {
         acc[q].x -= (sx[q][0] + sx[q][1]) + (sx[q][2] + sx[q][3]);
         acc[q].y -= (sy[q][0] + sy[q][1]) + (sy[q][2] + sy[q][3]);
+        if (E != 0) {  // block-uniform
+          acc[q].x *= cscale;
+          acc[q].y *= cscale;
+        }
         nn += acc[q].x * acc[q].x + acc[q].y * acc[q].y;
       }
     if (packed) {
@@ -627,7 +649,9 @@ __global__ void __launch_bounds__(kRedThreads) k_arn_axpy(TB* __restrict__ V, lo
     for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
     if (threadIdx.x == 0) {
       A.cnt[r] = 0;
-      const double nw2 = nonneg(sc[j] * sc[j] * t);  // |w'|^2 at true scale
+      const double us = ldexp(u, E);  // scale of the stored W_{j+1}: u / c
+      sc[j + 1] = us;
+      const double nw2 = nonneg(us * us * t);  // |w'|^2 at true scale
       nw2s = nw2;
       fin = 1;
       if (pass == 0 && nw2 < 0.0625 * S->wn2) {
@@ -658,7 +682,8 @@ __global__ void k_arn_init(ArnLayout A, const double* __restrict__ init, int nb)
   S->stop = stop;
   S->wn2 = 0.0;
   S->beta = beta;
-  A.sc[(long long)r * (m + 2)] = 1.0;
+  A.sc[(long long)r * (m + 2)] = 1.0;      // W_0: the normalised residual
+  A.sc[(long long)r * (m + 2) + 1] = 1.0;  // W_1 = A W_0 before its projection
   double2* g = A.gv + (long long)r * (m + 1);
   g[0] = make_double2(beta, 0.0);
   A.cnt[r] = 0;

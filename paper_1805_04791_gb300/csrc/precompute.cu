@@ -28,12 +28,66 @@ __global__ void k_twiddle(V* tw, int M) {
   tw[j].y = -s;
 }
 
-vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st) {
-  VIE_CK(dalloc((void**)t64, sizeof(double2) * M, st));
-  VIE_CK(dalloc((void**)t32, sizeof(float2) * M, st));
-  k_twiddle<double2><<<(M + 127) / 128, 128, 0, st>>>(*t64, M);
-  k_twiddle<float2><<<(M + 127) / 128, 128, 0, st>>>(*t32, M);
+// exp(-2 pi i num / den) for 0 <= num < den: the quarter turns are taken out
+// in integer arithmetic, the rest is an angle in [0, pi/2).
+static void exp_m2pi(long long num, long long den, double* c, double* s) {
+  const long long q = (4 * num) / den, rem = 4 * num - q * den;
+  const double t = M_PI * (double)rem / (2.0 * (double)den);
+  const double c0 = std::cos(t), s0 = std::sin(t);
+  double cc, ss;  // cos, sin of the full angle
+  switch (q & 3) {
+    case 0: cc = c0; ss = s0; break;
+    case 1: cc = -s0; ss = c0; break;
+    case 2: cc = -c0; ss = -s0; break;
+    default: cc = s0; ss = -c0; break;
+  }
+  *c = cc;
+  *s = -ss;
+}
+
+// Line table of a plan (line_table_len entries, layout of line_fft): the Q
+// twiddles exp(-2 pi i j / Q) on the device; for a Bluestein plan then the
+// chirps c-_j = exp(-pi i j^2 / M) and c+_j = conj(c-_j) with j^2 reduced mod
+// 2M, and H-_k = (1/Q) sum_{|j|<M} c+_j exp(-2 pi i j k / Q)
+//             = (1/Q) (1 + 2 sum_{0<j<M} c+_j cos(2 pi j k / Q)),
+// all in FP64 on the host.
+vie_status make_line_table(const FftPlan& pl, double2** t64, float2** t32, cudaStream_t st) {
+  const int M = pl.M, Q = pl.Q, len = line_table_len(pl);
+  VIE_CK(dalloc((void**)t64, sizeof(double2) * len, st));
+  VIE_CK(dalloc((void**)t32, sizeof(float2) * len, st));
+  k_twiddle<double2><<<(Q + 127) / 128, 128, 0, st>>>(*t64, Q);
+  k_twiddle<float2><<<(Q + 127) / 128, 128, 0, st>>>(*t32, Q);
   VIE_CK(cudaGetLastError());
+  if (Q == M) return VIE_OK;
+  std::vector<double2> h(len - Q);
+  std::vector<float2> h32(len - Q);
+  for (int j = 0; j < M; ++j) {
+    double c, sn;
+    exp_m2pi(((long long)j * j) % (2LL * M), 2LL * M, &c, &sn);
+    h[j] = make_double2(c, sn);
+    h[M + j] = make_double2(c, -sn);
+  }
+  std::vector<double> cq(Q);
+  for (int t = 0; t < Q; ++t) {
+    double c, sn;
+    exp_m2pi(t, Q, &c, &sn);
+    cq[t] = c;
+  }
+  for (int k = 0; k < Q; ++k) {
+    double re = 0.0, im = 0.0;
+    int jk = 0;  // j k mod Q
+    for (int j = 1; j < M; ++j) {
+      jk += k;
+      if (jk >= Q) jk -= Q;
+      re += h[M + j].x * cq[jk];
+      im += h[M + j].y * cq[jk];
+    }
+    h[2 * M + k] = make_double2((1.0 + 2.0 * re) / Q, 2.0 * im / Q);
+  }
+  for (size_t i = 0; i < h.size(); ++i) h32[i] = make_float2((float)h[i].x, (float)h[i].y);
+  VIE_CK(cudaMemcpyAsync(*t64 + Q, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice, st));
+  VIE_CK(cudaMemcpyAsync(*t32 + Q, h32.data(), sizeof(float2) * h32.size(), cudaMemcpyHostToDevice, st));
+  VIE_CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
   return VIE_OK;
 }
 
@@ -199,12 +253,12 @@ __global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan 
                            const typename CT<T>::V* __restrict__ twg, int nl) {
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int LS = M + 1;
+  const int Q = pl.Q, LS = Q + 1;
   V* tw = (V*)smraw;
-  V* b0 = tw + M;
+  V* b0 = tw + Q;
   V* b1 = b0 + nl * LS;
   const int tid = flat_tid(), nt = flat_nthreads();
-  for (int j = tid; j < M; j += nt) tw[j] = twg[j];
+  for (int j = tid; j < Q; j += nt) tw[j] = twg[j];
   const long long MM = (long long)M * M;
   // address of element j of tile line l
   auto addr = [&](int l, int j) -> long long {
@@ -218,7 +272,7 @@ __global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan 
     b0[l * LS + j] = to_v<T>(data[addr(l, j)]);
   }
   __syncthreads();
-  V* r = tile_fft<S, T>(b0, b1, pl, tw, nl, LS);
+  V* r = line_fft<S, T>(b0, b1, pl, tw, twg + Q, nl, LS);
   for (int idx = tid; idx < nl * M; idx += nt) {
     int l, j;
     if (axis == 0) { l = idx / M; j = idx - l * M; } else { j = idx / nl; l = idx - j * nl; }
@@ -226,9 +280,10 @@ __global__ void k_fft_cube(double2* __restrict__ data, int M, int axis, FftPlan 
   }
 }
 
-static int pick_nl(int M) {
+// Lines per tile: a power of two dividing M, with the tile within 200 KB.
+static int pick_nl(const FftPlan& pl, size_t vs) {
   int nl = 8;
-  while (nl > 1 && (M % nl != 0)) nl >>= 1;
+  while (nl > 1 && (pl.M % nl != 0 || vs * (pl.Q + 2 * (size_t)nl * (pl.Q + 1)) > 200 * 1024)) nl >>= 1;
   return nl;
 }
 
@@ -236,10 +291,23 @@ static int pick_nl(int M) {
 // T (FP64, or double-word on the FP32 pipes), one block row per tile line.
 template <int S, typename T>
 static vie_status fft_cube(double2* data, int M, const FftPlan& pl, const typename CT<T>::V* tw, cudaStream_t st) {
-  const int nl = pick_nl(M);
-  const size_t smem = sizeof(typename CT<T>::V) * (M + 2 * nl * (M + 1));
+  const size_t vs = sizeof(typename CT<T>::V);
+  const int nl = pick_nl(pl, vs);
+  const size_t smem = vs * (pl.Q + 2 * nl * (pl.Q + 1));
+  if (smem > (size_t)smem_optin_bytes()) {
+    set_error("set-up transform line too long for shared memory");
+    return VIE_EINVAL;
+  }
   VIE_CK(allow_smem(k_fft_cube<S, T>));
-  const dim3 blk(std::max(1, std::min(32, M / 16)), nl);
+  // threads per line: M/16 up to 32 for direct plans; a long Bluestein line
+  // (one to four per tile) one per 16 elements of Q, up to 128, and at most
+  // 256 threads per block
+  int tx = std::max(1, std::min(32, M / 16));
+  if (pl.Q != pl.M) {
+    tx = 32;
+    while (tx * 16 < pl.Q && tx < 128 && 2 * tx * nl <= 256) tx <<= 1;
+  }
+  const dim3 blk(tx, nl);
   for (int axis = 0; axis < 3; ++axis) {
     dim3 grid = axis == 0 ? dim3((unsigned)((long long)M * M / nl), 1) : dim3(M / nl, M);
     k_fft_cube<S, T><<<grid, blk, smem, st>>>(data, M, axis, pl, tw, nl);
@@ -330,6 +398,11 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
   double2* tab = nullptr;
   double2 *F = nullptr, *E = nullptr, *tw_sn = nullptr;
   float2* tw_sn32 = nullptr;
+  FftPlan plsn;
+  if (!make_line_plan(sn, &plsn)) {
+    set_error("bad oversampled grid size");
+    return VIE_EINVAL;
+  }
   const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = (long long)(n + 1) * (n + 1) * (n + 1);
   if (!P->sym_oct) VIE_CK(dalloc((void**)&P->sym_oct, sizeof(double2) * SYM_COUNT * O3, st));
   VIE_CK(dalloc((void**)&tab, sizeof(double2) * (jmax + 1), st));
@@ -337,7 +410,7 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
   VIE_CK(cudaGetLastError());
   VIE_CK(dalloc((void**)&F, sizeof(double2) * S3, st));
   VIE_CK(dalloc((void**)&E, sizeof(double2) * M3, st));
-  vie_status s = make_twiddles(sn, &tw_sn, &tw_sn32, st);
+  vie_status s = make_line_table(plsn, &tw_sn, &tw_sn32, st);
   if (s != VIE_OK) return s;
   // the kernel-transform FFTs run in double-word arithmetic (FP64 accuracy on
   // the FP32 pipes); VIE_SETUP_FP64=1 keeps them in native FP64
@@ -345,14 +418,9 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
   const bool dw = !(e64 && e64[0] == '1');
   cdf *tw_sndf = nullptr, *tw_2ndf = nullptr;
   if (dw) {
-    s = to_df(tw_sn, &tw_sndf, sn, st);
-    if (s == VIE_OK) s = to_df(P->tw64, &tw_2ndf, M, st);
+    s = to_df(tw_sn, &tw_sndf, line_table_len(plsn), st);
+    if (s == VIE_OK) s = to_df(P->tw64, &tw_2ndf, line_table_len(P->plan2n), st);
     if (s != VIE_OK) return s;
-  }
-  FftPlan plsn;
-  if (!make_plan(sn, &plsn)) {
-    set_error("bad oversampled grid size");
-    return VIE_EINVAL;
   }
   const int gb = 152 * 16;
   for (int sym = 0; sym < SYM_COUNT; ++sym) {
@@ -387,9 +455,11 @@ static const unsigned kDmask = (1u << SYM_DX) | (1u << SYM_DY) | (1u << SYM_DZ);
 static vie_status combine_sets(vie_problem* P, int which, cudaStream_t st);
 
 vie_status build_kernels(vie_problem* P, cudaStream_t st) {
-  // the operator needs -k_a k_b (and, for Maxwell, 1 and i k_a); the scattered
-  // field of Laplace/Helmholtz needs i k_a and is built on first use
-  const unsigned mask = P->kind == VIE_MAXWELL ? (kQmask | kDmask | (1u << SYM_1)) : kQmask;
+  // the operator needs -k_a k_b (and, for Maxwell, 1; with mu also the curl
+  // symbols i k_a); the symbols only the scattered field needs are built on
+  // its first use
+  unsigned mask = kQmask;
+  if (P->kind == VIE_MAXWELL) mask |= (1u << SYM_1) | (P->has_mu ? kDmask : 0u);
   vie_status s = compute_symbols(P, mask, st);
   if (s != VIE_OK) return s;
   return combine_sets(P, 0, st);
@@ -512,7 +582,7 @@ vie_status build_df(vie_problem* P, cudaStream_t st) {
   const long long N = (long long)P->n * P->n * P->n;
   const long long O3 = (long long)(P->n + 1) * (P->n + 1) * (P->n + 1);
   vie_status s = VIE_OK;
-  if (!P->twdf) s = to_df(P->tw64, &P->twdf, 2 * P->n, st);
+  if (!P->twdf) s = to_df(P->tw64, &P->twdf, line_table_len(P->plan2n), st);
   if (s == VIE_OK && !P->Hedf) s = to_df(P->He64, &P->Hedf, 6 * N, st);
   if (s == VIE_OK && P->Hm64 && !P->Hmdf) s = to_df(P->Hm64, &P->Hmdf, 6 * N, st);
   if (s == VIE_OK) s = to_df(P->kapply.oct64, &P->kapply.octdf, (long long)P->kapply.narr * O3, st);

@@ -1,7 +1,8 @@
 // Device-side building blocks shared by every kernel of the library:
 // complex arithmetic on CUDA vector types, small DFT codelets, and a
 // shared-memory mixed-radix (2, 3, 4, 5, 7, 8, 11, 16) Stockham FFT that
-// transforms a tile of lines resident in shared memory.
+// transforms a tile of lines resident in shared memory; line lengths with a
+// larger prime factor go through Bluestein's chirp-z algorithm on top of it.
 //
 // The FFT is the engine of the truncated-kernel method of Sec. 5 (steps a-c:
 // truncate the Green's function, transform it, cut off at the grid Nyquist
@@ -499,18 +500,23 @@ template <int S, typename T> struct Dft<7, S, T> : DftOdd<7, S, T> {};
 template <int S, typename T> struct Dft<11, S, T> : DftOdd<11, S, T> {};
 
 // ------------------------------------------------------------ FFT plan
+// A line DFT of length M runs as radix stages of length Q.  Q = M when M
+// factors into the codelet radices; otherwise Q is the smallest such length
+// with Q >= 2M - 1 and the DFT is Bluestein's chirp-z convolution (line_fft).
 struct FftPlan {
   int M;      // transform length
-  int ns;     // number of stages
+  int Q;      // length of the radix-stage transform (M, or Bluestein's padded length)
+  int ns;     // number of stages of the length-Q transform
   int R[8];   // radices, first stage first
 };
 
-// Factor M = 2^a 3^b 5^c 7^d 11^e into radices 16, 8, 4, 2, 3, 5, 7, 11;
-// returns false if M has other factors.
-inline bool make_plan(int M, FftPlan* pl) {
-  pl->M = M;
+// Factor Q = 2^a 3^b 5^c 7^d 11^e into radices 16, 8, 4, 2, 3, 5, 7, 11 as a
+// direct plan of length M = Q; returns false if Q has other factors.
+inline bool make_plan(int Q, FftPlan* pl) {
+  pl->M = Q;
+  pl->Q = Q;
   pl->ns = 0;
-  int m = M;
+  int m = Q;
   const int rad[8] = {16, 8, 4, 2, 3, 5, 7, 11};
   for (int k = 0; k < 8; ++k)
     while (m % rad[k] == 0 && m > 1) {
@@ -518,8 +524,25 @@ inline bool make_plan(int M, FftPlan* pl) {
       pl->R[pl->ns++] = rad[k];
       m /= rad[k];
     }
-  return m == 1 && M >= 2;
+  return m == 1 && Q >= 2;
 }
+
+// Plan of a length-M line DFT for any M >= 2: direct when M is smooth, else
+// Bluestein with the smallest smooth Q >= 2M - 1.
+inline bool make_line_plan(int M, FftPlan* pl) {
+  if (M < 2) return false;
+  if (make_plan(M, pl)) return true;
+  for (int Q = 2 * M - 1; Q <= 8 * M; ++Q)
+    if (make_plan(Q, pl)) {
+      pl->M = M;
+      return true;
+    }
+  return false;
+}
+
+// Entries of a plan's line table: the Q twiddles exp(-2 pi i j / Q), and for a
+// Bluestein plan also the chirps and the transformed chirp kernel.
+inline int line_table_len(const FftPlan& pl) { return pl.Q == pl.M ? pl.M : 2 * pl.Q + 2 * pl.M; }
 
 // One Stockham stage of radix R over nl lines of length M stored at stride ls.
 // Butterfly i of a line reads in[i + r M/R] (r < R), twiddles by
@@ -555,9 +578,10 @@ __device__ __forceinline__ void stage(const typename CT<T>::V* __restrict__ in, 
   }
 }
 
-// Transform nl lines held in buffer a (stride ls) in place-of-ping-pong with b.
-// Must be called by every thread of the block after the data is in a and
-// synchronised.  Returns the buffer that holds the result (synchronised).
+// Length-Q transform (the radix stages of the plan) of nl lines held in buffer
+// a (stride ls) in place-of-ping-pong with b.  Must be called by every thread
+// of the block after the data is in a and synchronised.  Returns the buffer
+// that holds the result (synchronised).
 template <int S, typename T>
 __device__ typename CT<T>::V* tile_fft(typename CT<T>::V* a, typename CT<T>::V* b, const FftPlan& pl,
                                        const typename CT<T>::V* tw, int nl, int ls) {
@@ -565,14 +589,14 @@ __device__ typename CT<T>::V* tile_fft(typename CT<T>::V* a, typename CT<T>::V* 
   for (int s = 0; s < pl.ns; ++s) {
     const int R = pl.R[s];
     switch (R) {
-      case 16: stage<16, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      case 8: stage<8, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      case 4: stage<4, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      case 2: stage<2, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      case 3: stage<3, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      case 5: stage<5, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      case 7: stage<7, S, T>(a, b, pl.M, p, tw, nl, ls); break;
-      default: stage<11, S, T>(a, b, pl.M, p, tw, nl, ls); break;
+      case 16: stage<16, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      case 8: stage<8, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      case 4: stage<4, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      case 2: stage<2, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      case 3: stage<3, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      case 5: stage<5, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      case 7: stage<7, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
+      default: stage<11, S, T>(a, b, pl.Q, p, tw, nl, ls); break;
     }
     __syncthreads();
     typename CT<T>::V* t = a;
@@ -585,5 +609,53 @@ __device__ typename CT<T>::V* tile_fft(typename CT<T>::V* a, typename CT<T>::V* 
 
 __device__ __forceinline__ int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int flat_nthreads() { return blockDim.x * blockDim.y; }
+
+// Length-M DFT  X_k = sum_{j<M} x_j exp(S 2 pi i j k / M)  of nl lines whose
+// first M entries are in buffer a (stride ls >= Q + 1), ping-pong with b (same
+// shape); tw holds the Q twiddles of the plan, bt the rest of its line table.
+// Same calling rules and result as tile_fft; the entries k >= M of the result
+// lines are scratch.
+//
+// Bluestein's chirp-z identity: with c_j = exp(S pi i j^2 / M), 2 j k = j^2 +
+// k^2 - (k - j)^2 gives X_k = c_k sum_j (x_j c_j) conj(c_{k-j}), a linear
+// convolution of length 2M - 1 evaluated as a circular one of length Q:
+//   a = (x c, 0, ..., 0),  X = c * F+( F-(a) * H ) on k < M,
+// where F-/F+ are the unnormalised length-Q transforms of sign -/+ and
+// H = F-(conj c placed at j and Q - j for |j| < M) / Q is tabulated.  The
+// chirp angles are reduced exactly (j^2 mod 2M) when the table is made.
+// Table bt: c for S = -1 (M entries), c for S = +1 (M), H for S = -1 (Q);
+// H for S = +1 is its complex conjugate (the chirp kernel is even).
+template <int S, typename T>
+__device__ typename CT<T>::V* line_fft(typename CT<T>::V* a, typename CT<T>::V* b, const FftPlan& pl,
+                                       const typename CT<T>::V* tw, const typename CT<T>::V* __restrict__ bt, int nl,
+                                       int ls) {
+  typedef typename CT<T>::V V;
+  if (pl.Q == pl.M) return tile_fft<S, T>(a, b, pl, tw, nl, ls);
+  const int M = pl.M, Q = pl.Q;
+  const V* __restrict__ ch = bt + (S < 0 ? 0 : M);
+  const V* __restrict__ hh = bt + 2 * M;
+  const int tid = flat_tid(), nt = flat_nthreads();
+  for (int idx = tid; idx < nl * Q; idx += nt) {
+    const int l = idx / Q, j = idx - l * Q;
+    V& v = a[l * ls + j];
+    v = (j < M) ? cmul(v, ch[j]) : CT<T>::make(0, 0);
+  }
+  __syncthreads();
+  V* r = tile_fft<-1, T>(a, b, pl, tw, nl, ls);
+  for (int idx = tid; idx < nl * Q; idx += nt) {
+    const int l = idx / Q, k = idx - l * Q;
+    V& v = r[l * ls + k];
+    v = (S < 0) ? cmul(v, hh[k]) : cmulc(v, hh[k]);
+  }
+  __syncthreads();
+  r = tile_fft<+1, T>(r, (r == a) ? b : a, pl, tw, nl, ls);
+  for (int idx = tid; idx < nl * M; idx += nt) {
+    const int l = idx / M, k = idx - l * M;
+    V& v = r[l * ls + k];
+    v = cmul(v, ch[k]);
+  }
+  __syncthreads();
+  return r;
+}
 
 }  // namespace vie

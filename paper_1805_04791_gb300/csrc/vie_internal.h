@@ -71,8 +71,8 @@ struct vie_problem {
   double lo = 0, hi = 0, D = 0, h = 0, L = 0, omega = 0;
   int device = 0;
   cudaStream_t stream = nullptr;  // home stream: memory is freed stream-ordered on it at destroy
-  vie::FftPlan plan2n;
-  double2* tw64 = nullptr;   // exp(-2 pi i j / 2n), j < 2n
+  vie::FftPlan plan2n;       // length-2n line DFT (Bluestein's algorithm when 2n is not smooth)
+  double2* tw64 = nullptr;   // its line table: exp(-2 pi i j / Q), j < Q, then the Bluestein tables
   float2* tw32 = nullptr;
   double2* He64 = nullptr;   // [6][n^3] symmetric H_eps (xx yy zz xy xz yz)
   float2* He32 = nullptr;
@@ -128,7 +128,7 @@ size_t grid_vec_bytes(const vie_problem* P, int c, int nrhs, size_t elem);
 vie_status build_medium(vie_problem* P, const void* eps, const void* mu, cudaStream_t st);
 vie_status build_kernels(vie_problem* P, cudaStream_t st);
 vie_status build_eval_kernels(vie_problem* P, cudaStream_t st);
-vie_status make_twiddles(int M, double2** t64, float2** t32, cudaStream_t st);
+vie_status make_line_table(const FftPlan& pl, double2** t64, float2** t32, cudaStream_t st);
 // Double-word copies of the twiddles, medium tensors and apply kernels (idempotent).
 vie_status build_df(vie_problem* P, cudaStream_t st);
 

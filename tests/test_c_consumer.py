@@ -26,7 +26,7 @@ int main(void) {
          vie_problem_bytes(VIE_HELMHOLTZ, 128, 1, 50, 0), vie_problem_bytes(VIE_MAXWELL, 128, 1, 50, 1));
   /* refusals that return before touching a device */
   vie_problem* P = (vie_problem*)0;
-  vie_status s1 = vie_problem_create(VIE_LAPLACE, 13, -1.0, 1.0, 0.0, (const void*)0, (const void*)0, (void*)0, &P);
+  vie_status s1 = vie_problem_create(VIE_LAPLACE, 3, -1.0, 1.0, 0.0, (const void*)0, (const void*)0, (void*)0, &P);
   const char* m1 = vie_last_error();
   char msg1[256];
   strncpy(msg1, m1, sizeof msg1 - 1);

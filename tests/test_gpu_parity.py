@@ -264,7 +264,7 @@ def test_invalid_arguments(vie):
 
     p = vi.laplace_bump_problem(n=8)
     e = eps_dev(p)
-    for bad in [dict(n=3), dict(n=13), dict(n=26), dict(n=512), dict(lo=1.0, hi=1.0), dict(omega=-1.0)]:
+    for bad in [dict(n=3), dict(n=-4), dict(n=513), dict(lo=1.0, hi=1.0), dict(omega=-1.0)]:
         kw = dict(kind=vie.VIE_LAPLACE, n=8, lo=-1.0, hi=1.0, omega=0.0)
         kw.update(bad)
         with pytest.raises(vie.VieError) as ei:

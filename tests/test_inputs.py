@@ -61,3 +61,23 @@ def test_paper_media_follow_their_definitions():
     w = W[i]
     D = np.diag([1 + w, 1 + 2 * w, 1 + 3 * w])
     assert np.allclose(dense[:, :, i[0], i[1], i[2]].real, R2 @ R1 @ D @ R1.T @ R2.T, atol=1e-14)
+
+
+def test_oscillatory_medium_follows_its_definition():
+    """Eq. (1stEx): (1 + W (1 + 0.1 sin(w x) sin(w y) sin(w z))) I; the device-side
+    builder gives the same samples as the host one."""
+    import torch
+
+    n, w = 9, 40.0
+    eps = vi.oscillatory_eps(n, w)
+    i = (1, 4, 7)  # (z, y, x)
+    t = vi.grid_nodes(n, 0.0, 1.0)
+    z, y, x = t[i[0]], t[i[1]], t[i[2]]
+    f = lambda s: np.exp(-(((s - 0.5) / 0.25) ** 8))
+    v = 1.0 + f(x) * f(y) * f(z) * (1.0 + 0.1 * np.sin(w * x) * np.sin(w * y) * np.sin(w * z))
+    assert np.allclose(eps[:, :, i[0], i[1], i[2]], v * np.eye(3), rtol=0, atol=1e-15)
+    et = vi.oscillatory_eps_torch(n, "cpu", w).numpy()
+    assert np.allclose(et, eps.reshape(9, -1), rtol=0, atol=1e-15)
+    p = vi.oscillatory_problem(n, w)
+    assert p.kind == "maxwell" and p.mu is None and (p.lo, p.hi, p.omega) == (0.0, 1.0, w)
+    assert np.array_equal(p.directions[0], [1.0, 0.0, 0.0]) and np.array_equal(p.polarisations[0], [0.0, 0.0, 1.0])

@@ -283,6 +283,25 @@ def paper_medium(name: str, n: int, lo=0.0, hi=1.0) -> np.ndarray:
     raise ValueError(name)
 
 
+def oscillatory_eps(n: int, omega: float = 408.0, lo=0.0, hi=1.0) -> np.ndarray:
+    """(1 + W (1 + 0.1 sin(omega x) sin(omega y) sin(omega z))) I, the isotropic
+    oscillatory medium of the first experiment of Sec. 5.2 (Eq. (1stEx))."""
+    Z, Y, X = grid_coords(n, lo, hi)
+    s = 1.0 + bump_W(n, lo, hi) * (1.0 + 0.1 * np.sin(omega * X) * np.sin(omega * Y) * np.sin(omega * Z))
+    eps = np.zeros((3, 3, n, n, n), np.complex128)
+    for a in range(3):
+        eps[a, a] = s
+    return eps
+
+
+def oscillatory_problem(n: int, omega: float = 408.0) -> Problem:
+    """Reduced Maxwell (mu = I) on [0,1]^3 with ``oscillatory_eps`` and the incident
+    wave E^in = (0, 0, exp(i omega x)) of the first experiment of Sec. 5.2."""
+    return Problem("maxwell", n, 0.0, 1.0, omega, oscillatory_eps(n, omega), None,
+                   np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 0.0, 1.0]]),
+                   meta={"workload": f"maxwell_oscillatory_{n}", "omega": omega})
+
+
 def random_field(n: int, c: int, seed: int, nrhs: int = 1) -> np.ndarray:
     """Seeded complex Gaussian test vector of shape (nrhs, c, n, n, n) (numpy generator)."""
     g = np.random.default_rng(seed)
@@ -324,6 +343,23 @@ def bump_medium_torch(n: int, seed: int, device, lo=-1.0, hi=1.0, amp=0.5, width
     for a in range(3):
         for b in range(3):
             eps[3 * a + b] = amp * float(S[a, b]) * g + (1.0 if a == b else 0.0)
+    return eps
+
+
+def oscillatory_eps_torch(n: int, device, omega: float = 408.0, lo=0.0, hi=1.0):
+    """[9][n^3] complex128 torch tensor of ``oscillatory_eps`` built on the device
+    (at n = 326 the host array would be 5 GB)."""
+    import torch
+
+    t = torch.as_tensor(grid_nodes(n, lo, hi), dtype=torch.float64, device=device)
+    f = torch.exp(-(((t - 0.5) / 0.25) ** 8))
+    sw = torch.sin(omega * t)
+    W = (f[:, None, None] * f[None, :, None] * f[None, None, :]).reshape(-1)
+    osc = (sw[:, None, None] * sw[None, :, None] * sw[None, None, :]).reshape(-1)
+    s = 1.0 + W * (1.0 + 0.1 * osc)
+    eps = torch.zeros((9, n * n * n), dtype=torch.complex128, device=device)
+    for a in range(3):
+        eps[4 * a] = s
     return eps
 
 
