@@ -422,50 +422,59 @@ def leg_maxwell256(args, dev):
 
 def leg_maxwell326(args, dev):
     """The first experiment of Sec. 5.2 at its coarse grid: reduced Maxwell (mu = I)
-    at 326^3 on [0,1]^3, eps = (1 + W (1 + 0.1 sin(w x) sin(w y) sin(w z))) I with
-    w = 408, E^in = (0, 0, exp(i w x)).  2n = 652 = 4 x 163 and 3n = 978 = 6 x 163:
-    every transform runs Bluestein's algorithm (padded lengths 1320 and 1960).
-    Set-up time, FP32 apply time, and a mixed solve to 1e-8."""
+    at 326^3 on [0,1]^3, eps = (1 + W (1 + 0.1 sin(w x) sin(w y) sin(w z))) I,
+    E^in = (0, 0, exp(i w x)).  2n = 652 = 4 x 163: the apply runs on the padded
+    convolution grid 660, the set-up's 3n = 978 lines take Bluestein's algorithm
+    (padded length 1960).  At the printed w = 408 the operator's GMRES
+    iteration count is far above the paper's 61 matvecs (on the oracle it grows
+    about linearly with w), so that solve runs a capped number of iterations
+    and reports the residual reached; the same medium at w = 51 (8 wavelengths
+    across the box) is solved to 1e-8.  Set-up, FP32 apply and solve times."""
     import torch
 
     import paper_1805_04791_gb300 as vie
     import vie_inputs as vi
 
-    n, w = 326, 408.0
-    eps = vi.oscillatory_eps_torch(n, dev, w)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    P = vie.Problem("maxwell", n, 0.0, 1.0, w, eps, None)
-    t_setup = time.perf_counter() - t0
-    del eps
-    torch.cuda.empty_cache()
-    b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
-    P.rhs(np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0]), 1, b)
-    out = {"workload": f"maxwell_oscillatory_{n}", "omega": w, "setup_s": t_setup,
-           "padded_lengths": {"2n": 1320, "3n": 1960}}
-    x32 = b.to(torch.complex64)
-    y32 = torch.empty_like(x32)
-    P.apply(x32, y32, vie.VIE_FP32)
-    torch.cuda.synchronize()
-    reps = 5
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
+    n = 326
+    out = {"workload": f"maxwell_oscillatory_{n}", "conv_grid": 660, "setup_bluestein_Q": 1960, "cases": {}}
+    for w, kw in ((51.0, dict(tol=1e-8, max_inner=600)), (408.0, dict(tol=1e-8, max_inner=300))):
+        eps = vi.oscillatory_eps_torch(n, dev, w)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P = vie.Problem("maxwell", n, 0.0, 1.0, w, eps, None)
+        t_setup = time.perf_counter() - t0
+        del eps
+        torch.cuda.empty_cache()
+        b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
+        P.rhs(np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0]), 1, b)
+        case = {"omega": w, "setup_s": t_setup}
+        x32 = b.to(torch.complex64)
+        y32 = torch.empty_like(x32)
         P.apply(x32, y32, vie.VIE_FP32)
-    e1.record()
-    torch.cuda.synchronize()
-    out["apply_fp32_ms"] = e0.elapsed_time(e1) / reps
-    del x32, y32
-    J = torch.zeros_like(b)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, info = P.solve(b, J, tol=1e-8, restart=50, max_outer=40, max_inner=600, inner_tol=1e-5,
-                       mode=vie.VIE_SOLVE_MIXED, allow_noconv=True)
-    torch.cuda.synchronize()
-    out["mixed"] = {"seconds": time.perf_counter() - t0, "status": int(st), "rel_residual": info.rel_residual,
-                    "applies_fp32": info.applies_fp32, "applies_fp64": info.applies_fp64,
-                    "gmres_iters": info.inner_iters}
-    P.close()
+        torch.cuda.synchronize()
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            P.apply(x32, y32, vie.VIE_FP32)
+        e1.record()
+        torch.cuda.synchronize()
+        case["apply_fp32_ms"] = e0.elapsed_time(e1) / reps
+        del x32, y32
+        J = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = P.solve(b, J, restart=50, max_outer=40, inner_tol=1e-5, mode=vie.VIE_SOLVE_MIXED,
+                           allow_noconv=True, **kw)
+        torch.cuda.synchronize()
+        case["mixed"] = {"seconds": time.perf_counter() - t0, "status": int(st), "tol": kw["tol"],
+                         "max_inner": kw["max_inner"], "rel_residual": info.rel_residual,
+                         "applies_fp32": info.applies_fp32, "applies_fp64": info.applies_fp64,
+                         "gmres_iters": info.inner_iters}
+        out["cases"][f"omega_{int(w)}"] = case
+        P.close()
+        del b, J
+        torch.cuda.empty_cache()
     return out
 
 

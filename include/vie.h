@@ -131,18 +131,21 @@ typedef struct {
 /* Create a problem: grid, medium and frequency (Sec. 2 / Eq. (Laplace_Scalar),
  * Sec. 3 / Eq. (Helmholtz0), Sec. 4 / Eq. (Maxwell)).
  *   kind   vie_kind.
- *   n      points per axis, 4 <= n <= 512 (register-resident kernels for 2n in
- *          {64, 96, 128, 192, 256, 384, 512}, shared-memory Stockham kernels for
- *          the other sizes; a line length 2n or 3n with a prime factor above 11
- *          is transformed by Bluestein's chirp-z algorithm over a padded length
- *          Q >= 2 (2n) - 1 made of the factors 2, 3, 5, 7, 11).  Odd n is valid:
- *          the oversampled set-up grid 3n is then odd and its frequency cut-off
- *          is the symmetric |m| <= (3n-1)/2, with no Nyquist entry.  The set-up
- *          holds (3n)^3 + (2n)^3 FP64 complex transform buffers (about 100 GB
- *          at n = 512); a failed allocation returns VIE_ENOMEM.  Applies whose
- *          z-pass tile of c lines of length Q + 1 (16 bytes per element in FP64
- *          and double-word arithmetic) exceeds shared memory return VIE_EINVAL:
- *          with c = 6 that is 2n above ~550 when 2n needs Bluestein's algorithm.
+ *   n      points per axis, 4 <= n <= 512.  The convolution grid is M = 2 nk
+ *          per axis with nk = n when n = 2^a 3^b 5^c 7^d 11^e, else the smallest
+ *          such nk > n (a circular convolution of length M >= 2n - 1 equals the
+ *          zero-padded one on the n^3 nodes; n = 326 runs on M = 660).
+ *          Register-resident kernels for M = 2n in {64, 96, 128, 192, 256, 384,
+ *          512}, shared-memory Stockham kernels for the other grids.  The
+ *          oversampled set-up grid is 3n; when 3n has a prime factor above 11
+ *          its lines are transformed by Bluestein's chirp-z algorithm over a
+ *          padded length Q >= 2 (3n) - 1 made of the factors 2, 3, 5, 7, 11.
+ *          Odd n is valid: the set-up grid 3n is then odd and its frequency
+ *          cut-off is the symmetric |m| <= (3n-1)/2, with no Nyquist entry.
+ *          The set-up holds (3n)^3 + M^3 FP64 complex transform buffers (about
+ *          75 GB at n = 512); a failed allocation returns VIE_ENOMEM.  M <= 1024
+ *          for every valid n, so the generic z-pass tile (six lines of M + 1
+ *          elements at 16 bytes, FP64) fits in shared memory.
  *   lo, hi box [lo, hi]^3 (hi > lo).
  *   omega  angular frequency (ignored for Laplace; >= 0).
  *   eps    device, FP64 complex [9][n][n][n], the 3x3 tensor row-major per node;

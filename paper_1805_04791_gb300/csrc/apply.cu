@@ -2,13 +2,17 @@
 // and the scattered-field evaluation, as a pruned zero-padded 3D convolution
 // (Sec. 5: the truncated kernel transform applied with the FFT).
 //
-// Five passes over HBM.  For 2n in {64, 96, 128, 192, 256, 384, 512} they are the
-// register-resident kernels of apply_fast.cuh (chosen here, with the z-pass
-// autotuner); every other 2n, and the double-word passes without a fast
-// kernel, run the shared-memory Stockham kernels of this file (vie_fft.cuh,
-// with Bluestein's algorithm when 2n has a prime factor above 11):
-//   P1  x-lines: zero-pad n -> 2n, forward FFT          x [c][n][n][n]    -> A [c][n][n][2n]
-//   P2  y-lines: zero-pad, forward FFT                   A                 -> B [c][n][2n][2n]
+// The convolution grid has M = 2 nk points per axis: nk = n when 2n factors
+// into the codelet radices 2, 3, 5, 7, 11, else the smallest such nk > n (a
+// circular convolution of length M >= 2n - 1 equals the zero-padded linear one
+// on the n^3 output nodes; n = 326, 2n = 4 x 163, runs on M = 660).
+// Five passes over HBM.  For M = 2n in {64, 96, 128, 192, 256, 384, 512} they
+// are the register-resident kernels of apply_fast.cuh (chosen here, with the
+// z-pass autotuner); every other grid, and the double-word passes without a
+// fast kernel, run the shared-memory Stockham kernels of this file
+// (vie_fft.cuh):
+//   P1  x-lines: zero-pad n -> M, forward FFT           x [c][n][n][n]    -> A [c][n][n][M]
+//   P2  y-lines: zero-pad, forward FFT                   A                 -> B [c][n][M][M]
 //   P3  z-pencils of all components: zero-pad, forward FFT, per-k kernel
 //       mixing (3x3 symmetric, 6x6 Maxwell, divergence or E/H), inverse
 //       FFT, keep z < n                                  B                 -> B (in place)
@@ -16,9 +20,9 @@
 //   P5  x-lines of all components: inverse FFT, keep x < n, epilogue
 //       y = x + H u (u the convolution; H per node, 3x3 symmetric)  A      -> y
 // The padded z-planes z >= n are never stored (their input is zero and their
-// output is discarded).  The kernel arrays are octants of the (2n)^3 DFT with
-// the identity part of T, the sign and factor 2 of B, and the 1/(2n)^3 of the
-// inverse DFT folded in.
+// output is discarded).  The kernel arrays are octants (nk + 1)^3 of the M^3
+// DFT with the identity part of T, the sign and factor 2 of B, and the 1/M^3
+// of the inverse DFT folded in.
 #include <algorithm>
 #include <cstdlib>
 #include <map>
@@ -27,10 +31,10 @@
 #include "apply_fast.cuh"
 
 namespace vie {
-// Generic kernels (any 2n): shared-memory Stockham passes with the twiddle
-// table staged in shared memory, and Bluestein's algorithm on top of them when
-// 2n has a prime factor above 11 (line_fft, vie_fft.cuh).  Tile lines have
-// the plan's inner length Q (= 2n for smooth sizes) plus one.
+// Generic kernels (any line plan): shared-memory Stockham passes with the
+// twiddle table staged in shared memory (line_fft, vie_fft.cuh; the apply's
+// plans are direct, Bluestein's algorithm is taken by the set-up's 3n lines).
+// Tile lines have the plan's inner length Q (= M for a direct plan) plus one.
 // ---------------------------------------------------------------- P1
 template <typename T>
 __global__ void k_p1(const typename IOT<T>::E* __restrict__ x, typename CT<T>::V* __restrict__ A, int n, FftPlan pl,
@@ -97,15 +101,16 @@ __global__ void k_py(const typename CT<T>::V* __restrict__ in, typename CT<T>::V
 }
 
 // ---------------------------------------------------------------- P3
+// Kernel value at (kz, ky, kx) of the M = 2 nk grid from its octant (nk + 1)^3.
 template <typename V>
 __device__ __forceinline__ V kval(const V* __restrict__ K, int a, long long O3, int O, int par, int kz, int ky,
-                                  int kx, int n) {
-  const int M = 2 * n;
+                                  int kx, int nk) {
+  const int M = 2 * nk;
   int sgn = 1;
   int oz = kz, oy = ky, ox = kx;
-  if (kz > n) { oz = M - kz; if (par & 4) sgn = -sgn; }
-  if (ky > n) { oy = M - ky; if (par & 2) sgn = -sgn; }
-  if (kx > n) { ox = M - kx; if (par & 1) sgn = -sgn; }
+  if (kz > nk) { oz = M - kz; if (par & 4) sgn = -sgn; }
+  if (ky > nk) { oy = M - ky; if (par & 2) sgn = -sgn; }
+  if (kx > nk) { ox = M - kx; if (par & 1) sgn = -sgn; }
   V v = K[a * O3 + ((long long)oz * O + oy) * O + ox];
   return (sgn < 0) ? vneg(v) : v;
 }
@@ -113,6 +118,7 @@ __device__ __forceinline__ V kval(const V* __restrict__ K, int a, long long O3, 
 template <typename T>
 __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const typename CT<T>::V* __restrict__ twg,
                      int nl, int C, const typename CT<T>::V* __restrict__ K, int mode) {
+  const int nk = pl.M / 2;  // kernel half-size: the octants are (nk + 1)^3
   typedef typename CT<T>::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int M = pl.M, Q = pl.Q, LS = Q + 1;
@@ -139,7 +145,7 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
   V* fw = line_fft<-1, T>(b0, b1, pl, tw, twg + Q, cin * nl, LS);
   V* ob = (fw == b0) ? b1 : b0;
   // per-k mixing
-  const int O = n + 1;
+  const int O = nk + 1;
   const long long O3 = (long long)O * O * O;
   for (int idx = tid; idx < nl * M; idx += nt) {
     const int l = idx % nl, kz = idx / nl;
@@ -149,11 +155,11 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
     V o[6];
     if (mode == KM_DIV) {
       V acc = CT<T>::make(0, 0);
-      for (int a = 0; a < 3; ++a) acc = acc + cmul(kval(K, a, O3, O, sym_parity(6 + a), kz, ky, kx, n), u[a]);
+      for (int a = 0; a < 3; ++a) acc = acc + cmul(kval(K, a, O3, O, sym_parity(6 + a), kz, ky, kx, nk), u[a]);
       o[0] = acc;
     } else {
       V q[6];
-      for (int a = 0; a < 6; ++a) q[a] = kval(K, a, O3, O, sym_parity(a), kz, ky, kx, n);
+      for (int a = 0; a < 6; ++a) q[a] = kval(K, a, O3, O, sym_parity(a), kz, ky, kx, nk);
       // symmetric 3x3: [xx xy xz; xy yy yz; xz yz zz]
       const V qxx = q[0], qyy = q[1], qzz = q[2], qxy = q[3], qxz = q[4], qyz = q[5];
       o[0] = cmul(qxx, u[0]) + cmul(qxy, u[1]) + cmul(qxz, u[2]);
@@ -161,7 +167,7 @@ __global__ void k_p3(typename CT<T>::V* __restrict__ B, int n, FftPlan pl, const
       o[2] = cmul(qxz, u[0]) + cmul(qyz, u[1]) + cmul(qzz, u[2]);
       if (mode == KM_MAXWELL6 || mode == KM_EMRED) {
         V p[3];
-        for (int a = 0; a < 3; ++a) p[a] = kval(K, 6 + a, O3, O, sym_parity(6 + a), kz, ky, kx, n);
+        for (int a = 0; a < 3; ++a) p[a] = kval(K, 6 + a, O3, O, sym_parity(6 + a), kz, ky, kx, nk);
         // P x J
         const V pxj0 = cmul(p[1], u[2]) - cmul(p[2], u[1]);
         const V pxj1 = cmul(p[2], u[0]) - cmul(p[0], u[2]);
@@ -291,9 +297,9 @@ static vie_status check_tiles(const FftPlan& pl, size_t vs, int C) {
   return VIE_EINVAL;
 }
 
-size_t apply_workspace_bytes(int n, int c, int nrhs, int prec) {
+size_t apply_workspace_bytes(int n, int nk, int c, int nrhs, int prec) {
   const size_t esz = prec == VIE_FP32 ? sizeof(float2) : sizeof(double2);  // double-word complex is 16 bytes too
-  const size_t M = 2 * (size_t)n;
+  const size_t M = 2 * (size_t)nk;
   return esz * (size_t)nrhs * c * ((size_t)n * n * M + (size_t)n * M * M);
 }
 
@@ -301,6 +307,10 @@ size_t apply_workspace_bytes(int n, int c, int nrhs, int prec) {
 struct FastSel {
   bool p1 = false, py = false, p3 = false, p5 = false;
 };
+
+// Grid length of the register-resident kernels, which take n = M/2 data points
+// per line: 2n when the convolution grid is 2n, else 0 (no fast kernels).
+static int fast_grid(const vie_problem* P) { return P->nk == P->n ? 2 * P->n : 0; }
 
 static FastSel fast_select(int M, int mode, bool with_identity) {
   FastSel f;
@@ -327,7 +337,7 @@ static long long tune_key(const vie_problem* P, int prec, int mode) { return ((l
 
 bool p3_schedule_ready(vie_problem* P, const KernelSet& K, int prec) {
   if (prec == VIE_DF64) return true;                       // one fixed schedule
-  if (!fast_select(2 * P->n, K.mode, true).p3) return true;  // generic kernels
+  if (!fast_select(fast_grid(P), K.mode, true).p3) return true;  // generic kernels
   int& v = P->p3_variant[prec][K.mode];
   if (v >= 0) return true;
   if (getenv("VIE_P3_VARIANT")) return true;  // a forced variant is launched untimed
@@ -372,7 +382,7 @@ static vie_status tune_dispatch(vie_problem* P, const KernelSet& K, void* B, int
 
 vie_status ensure_apply_workspace(vie_problem* P, const KernelSet& K, int prec, int nrhs, cudaStream_t st) {
   const int C = std::max(cin_of(K.mode), cout_of(K.mode));
-  const size_t need = apply_workspace_bytes(P->n, C, nrhs, prec);
+  const size_t need = apply_workspace_bytes(P->n, P->nk, C, nrhs, prec);
   if (P->ws.bytes < need) {
     dfree(P->ws.buf, st);  // stream-ordered: earlier work on st completes first
     P->ws.buf = nullptr;
@@ -392,7 +402,7 @@ template <typename T>
 static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
                               bool with_identity, cudaStream_t st) {
   typedef typename CT<T>::V V;
-  const int n = P->n, M = 2 * n;
+  const int n = P->n, M = 2 * P->nk;
   const int cin = cin_of(K.mode), cout = cout_of(K.mode);
   const int C = std::max(cin, cout);
   {
@@ -403,7 +413,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
   V* B = A + (size_t)nrhs * C * n * n * M;
   const V* tw = Prec<T>::tw(P);
   const V* Kp = Prec<T>::K(K);
-  const FftPlan& pl = P->plan2n;
+  const FftPlan& pl = P->planM;
   const size_t vs = sizeof(V);
   {
     vie_status e = check_tiles(pl, vs, C);
@@ -419,7 +429,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
 
   // double-word arithmetic runs on the generic kernels only: its fully
   // unrolled register-resident variants take far too long to compile
-  FastSel fs = fast_select(M, K.mode, with_identity);
+  FastSel fs = fast_select(fast_grid(P), K.mode, with_identity);
   if (Prec<T>::id == VIE_DF64) {
     // double-word fast kernels exist for 2n = 256 and the operator's kernel sets
     // only; its register-resident P5 (254 registers, one CTA per SM) is slower
@@ -532,8 +542,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
 }
 
 vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant, cudaStream_t st) {
-  const int M = 2 * P->n;
-  if (prec == VIE_DF64 || !fast_select(M, K.mode, true).p3) {  // generic kernels: nothing to tune
+  if (prec == VIE_DF64 || !fast_select(fast_grid(P), K.mode, true).p3) {  // generic kernels: nothing to tune
     *variant = -1;
     return VIE_OK;
   }

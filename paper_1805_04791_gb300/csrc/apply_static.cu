@@ -62,7 +62,7 @@ extern "C" vie_status vie_apply_static(vie_problem* P, const void* x, void* y, i
   }
   const KernelSet& K = P->kapply;
   const int C = std::max(cin_of(K.mode), cout_of(K.mode));
-  const size_t need = apply_workspace_bytes(P->n, C, nrhs, precision);
+  const size_t need = apply_workspace_bytes(P->n, P->nk, C, nrhs, precision);
   if (need > kStaticScratchBytes) {
     set_error("vie_apply_static: this grid size, component count, precision and nrhs need " +
               std::to_string(need) + " bytes of scratch; the static array holds " +

@@ -63,6 +63,15 @@ size_t grid_vec_bytes(const vie_problem* P, int c, int nrhs, size_t elem) {
 // fails returns VIE_ENOMEM.
 static bool valid_size(int n) { return n >= 4 && n <= 512; }
 
+int conv_half(int n) {
+  for (int m = n;; ++m) {
+    int r = m;
+    for (int p : {2, 3, 5, 7, 11})
+      while (r % p == 0) r /= p;
+    if (r == 1) return m;
+  }
+}
+
 static void free_set(KernelSet& k, cudaStream_t st) {
   dfree(k.oct64, st);
   dfree(k.oct32, st);
@@ -148,7 +157,8 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
   P->omega = kind == VIE_LAPLACE ? 0.0 : omega;
   cudaGetDevice(&P->device);
   P->stream = st;
-  if (!make_line_plan(2 * n, &P->plan2n)) {
+  P->nk = conv_half(n);
+  if (!make_line_plan(2 * P->nk, &P->planM) || P->planM.Q != P->planM.M) {
     delete P;
     set_error("bad FFT size");
     return VIE_EINVAL;
@@ -156,7 +166,7 @@ vie_status vie_problem_create(int kind, int n, double lo, double hi, double omeg
   vie_status s = VIE_OK;
   cudaError_t e = dalloc((void**)&P->dflag, sizeof(int) * 4, st);
   if (e != cudaSuccess) s = cuda_fail(e, "cudaMalloc(flag)");
-  if (s == VIE_OK) s = make_line_table(P->plan2n, &P->tw64, &P->tw32, st);
+  if (s == VIE_OK) s = make_line_table(P->planM, &P->tw64, &P->tw32, st);
   if (s == VIE_OK) s = build_medium(P, eps, mu, st);
   if (s == VIE_OK) s = build_kernels(P, st);
   if (s == VIE_OK) {
@@ -252,17 +262,18 @@ vie_status vie_eval_scattered(vie_problem* P, const void* J, void* field_out, in
 size_t vie_problem_bytes(int kind, int n, int nrhs, int restart, int has_mu) {
   if (n < 1 || nrhs < 1 || restart < 1) return 0;
   const size_t N = (size_t)n * n * n;
-  const size_t O3 = (size_t)(n + 1) * (n + 1) * (n + 1);
+  const size_t nk = (size_t)conv_half(n);
+  const size_t O3 = (nk + 1) * (nk + 1) * (nk + 1);
   const int c = (kind == VIE_MAXWELL && has_mu) ? 6 : 3;
   const int nsym = kind == VIE_MAXWELL ? 10 : 9;
   size_t held = 144 * N * (has_mu ? 2 : 1);  // H: 6 entries, FP64 + FP32
   held += 16 * O3 * nsym;                    // raw symbol octants
   held += 24 * O3 * 18;                      // apply + eval kernel sets, FP64 + FP32
   held += 96 * N * (has_mu ? 2 : 1) + 16 * O3 * (kind == VIE_MAXWELL ? 9 : 6);  // double-word copies (mixed solve)
-  // set-up peak: oversampled (3n)^3 and (2n)^3 FP64 transform buffers
-  const size_t setup = held + 16 * (27 * N + 8 * N);
+  // set-up peak: oversampled (3n)^3 and convolution-grid (2nk)^3 FP64 transform buffers
+  const size_t setup = held + 16 * (27 * N + 8 * nk * nk * nk);
   // steady state: FP64 apply workspace, mixed-precision Krylov group
-  size_t steady = held + apply_workspace_bytes(n, c, nrhs, VIE_FP64);
+  size_t steady = held + apply_workspace_bytes(n, (int)nk, c, nrhs, VIE_FP64);
   steady += (size_t)nrhs * c * N * (8 * (size_t)(restart + 1) + 16 * 2 + 8);
   return setup > steady ? setup : steady;
 }

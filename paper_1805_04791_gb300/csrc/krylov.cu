@@ -1034,7 +1034,7 @@ static int pick_group(vie_problem* P, int nrhs, int m, bool mixed) {
   if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) return 1;
   freeb += P->ks.bytes + P->ws.bytes;  // our own workspaces are reusable
   const size_t per = group_bytes_per_rhs(L, m, mixed) +
-                     apply_workspace_bytes(P->n, std::max(cin_of(P->kapply.mode), cout_of(P->kapply.mode)), 1,
+                     apply_workspace_bytes(P->n, P->nk, std::max(cin_of(P->kapply.mode), cout_of(P->kapply.mode)), 1,
                                            VIE_FP64);
   long long nb = (long long)(0.8 * (double)freeb / (double)per);
   const char* cap = getenv("VIE_GROUP_MAX");

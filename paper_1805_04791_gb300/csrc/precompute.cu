@@ -316,15 +316,16 @@ static vie_status fft_cube(double2* data, int M, const FftPlan& pl, const typena
   return VIE_OK;
 }
 
-// e[(2n)^3] from the inverse-transformed F[(sn)^3]: offsets d in [-(n-1), n-1]
-// at index d mod 2n, index n left zero; scale folds the 1/(sn)^3 of the inverse DFT.
-__global__ void k_embed(const double2* __restrict__ F, double2* __restrict__ e, int n, int sn, double scale) {
-  const int M = 2 * n;
+// e[M^3] (M = 2 nk >= 2n) from the inverse-transformed F[(sn)^3]: offsets d in
+// [-(n-1), n-1] at index d mod M, indices n..M-n left zero; scale folds the
+// 1/(sn)^3 of the inverse DFT.
+__global__ void k_embed(const double2* __restrict__ F, double2* __restrict__ e, int n, int nk, int sn, double scale) {
+  const int M = 2 * nk;
   const long long tot = (long long)M * M * M;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
     const int ex = (int)(idx % M), ey = (int)((idx / M) % M), ez = (int)(idx / ((long long)M * M));
-    if (ex == n || ey == n || ez == n) {
+    if ((ex >= n && ex <= M - n) || (ey >= n && ey <= M - n) || (ez >= n && ez <= M - n)) {
       e[idx] = make_double2(0.0, 0.0);
       continue;
     }
@@ -335,8 +336,8 @@ __global__ void k_embed(const double2* __restrict__ F, double2* __restrict__ e, 
   }
 }
 
-__global__ void k_octant(const double2* __restrict__ E, double2* __restrict__ oct, int n) {
-  const int M = 2 * n, O = n + 1;
+__global__ void k_octant(const double2* __restrict__ E, double2* __restrict__ oct, int nk) {
+  const int M = 2 * nk, O = nk + 1;
   const long long tot = (long long)O * O * O;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -373,7 +374,7 @@ __global__ void k_combine(const double2* __restrict__ sym_oct, double2* __restri
 
 static vie_status combine(vie_problem* P, KernelSet& K, int mode, const CombineDesc& cd, double diag_add,
                           int diag_mask, cudaStream_t st) {
-  const long long O = P->n + 1, O3 = O * O * O;
+  const long long O = P->nk + 1, O3 = O * O * O;
   K.mode = mode;
   K.narr = cd.narr;
   VIE_CK(dalloc((void**)&K.oct64, sizeof(double2) * cd.narr * O3, st));
@@ -391,7 +392,7 @@ static vie_status to_df(const double2* src, cdf** dst, long long count, cudaStre
 static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st) {
   mask &= ~P->sym_mask;
   if (!mask) return VIE_OK;
-  const int n = P->n, sn = 3 * n, M = 2 * n;
+  const int n = P->n, sn = 3 * n, M = 2 * P->nk;
   const double dk = 2.0 * M_PI / (3.0 * P->D);
   const int jmax = 3 * (sn / 2) * (sn / 2);
   const double w = P->kind == VIE_LAPLACE ? 0.0 : P->omega;
@@ -403,7 +404,8 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
     set_error("bad oversampled grid size");
     return VIE_EINVAL;
   }
-  const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = (long long)(n + 1) * (n + 1) * (n + 1);
+  const long long O = P->nk + 1;
+  const long long S3 = (long long)sn * sn * sn, M3 = (long long)M * M * M, O3 = O * O * O;
   if (!P->sym_oct) VIE_CK(dalloc((void**)&P->sym_oct, sizeof(double2) * SYM_COUNT * O3, st));
   VIE_CK(dalloc((void**)&tab, sizeof(double2) * (jmax + 1), st));
   k_ghat_table<<<(jmax + 256) / 256, 256, 0, st>>>(tab, jmax, dk, w, P->L);
@@ -419,7 +421,7 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
   cdf *tw_sndf = nullptr, *tw_2ndf = nullptr;
   if (dw) {
     s = to_df(tw_sn, &tw_sndf, line_table_len(plsn), st);
-    if (s == VIE_OK) s = to_df(P->tw64, &tw_2ndf, line_table_len(P->plan2n), st);
+    if (s == VIE_OK) s = to_df(P->tw64, &tw_2ndf, line_table_len(P->planM), st);
     if (s != VIE_OK) return s;
   }
   const int gb = 152 * 16;
@@ -429,11 +431,11 @@ static vie_status compute_symbols(vie_problem* P, unsigned mask, cudaStream_t st
     VIE_CK(cudaGetLastError());
     s = dw ? fft_cube<+1, df>(F, sn, plsn, tw_sndf, st) : fft_cube<+1, double>(F, sn, plsn, tw_sn, st);
     if (s != VIE_OK) return s;
-    k_embed<<<gb, 256, 0, st>>>(F, E, n, sn, 1.0 / (double)S3);
+    k_embed<<<gb, 256, 0, st>>>(F, E, n, P->nk, sn, 1.0 / (double)S3);
     VIE_CK(cudaGetLastError());
-    s = dw ? fft_cube<-1, df>(E, M, P->plan2n, tw_2ndf, st) : fft_cube<-1, double>(E, M, P->plan2n, P->tw64, st);
+    s = dw ? fft_cube<-1, df>(E, M, P->planM, tw_2ndf, st) : fft_cube<-1, double>(E, M, P->planM, P->tw64, st);
     if (s != VIE_OK) return s;
-    k_octant<<<gb, 256, 0, st>>>(E, P->sym_oct + (long long)sym * O3, n);
+    k_octant<<<gb, 256, 0, st>>>(E, P->sym_oct + (long long)sym * O3, P->nk);
     VIE_CK(cudaGetLastError());
   }
   dfree(F, st);
@@ -474,7 +476,7 @@ vie_status build_eval_kernels(vie_problem* P, cudaStream_t st) {
 }
 
 static vie_status combine_sets(vie_problem* P, int which, cudaStream_t st) {
-  const int n = P->n, M = 2 * n;
+  const int M = 2 * P->nk;
   const long long M3 = (long long)M * M * M;
   const double w = P->kind == VIE_LAPLACE ? 0.0 : P->omega;
   vie_status s = VIE_OK;
@@ -580,9 +582,9 @@ static vie_status to_df(const double2* src, cdf** dst, long long count, cudaStre
 vie_status build_df(vie_problem* P, cudaStream_t st) {
   if (P->kapply.octdf) return VIE_OK;
   const long long N = (long long)P->n * P->n * P->n;
-  const long long O3 = (long long)(P->n + 1) * (P->n + 1) * (P->n + 1);
+  const long long O3 = (long long)(P->nk + 1) * (P->nk + 1) * (P->nk + 1);
   vie_status s = VIE_OK;
-  if (!P->twdf) s = to_df(P->tw64, &P->twdf, line_table_len(P->plan2n), st);
+  if (!P->twdf) s = to_df(P->tw64, &P->twdf, line_table_len(P->planM), st);
   if (s == VIE_OK && !P->Hedf) s = to_df(P->He64, &P->Hedf, 6 * N, st);
   if (s == VIE_OK && P->Hm64 && !P->Hmdf) s = to_df(P->Hm64, &P->Hmdf, 6 * N, st);
   if (s == VIE_OK) s = to_df(P->kapply.oct64, &P->kapply.octdf, (long long)P->kapply.narr * O3, st);

@@ -71,8 +71,13 @@ struct vie_problem {
   double lo = 0, hi = 0, D = 0, h = 0, L = 0, omega = 0;
   int device = 0;
   cudaStream_t stream = nullptr;  // home stream: memory is freed stream-ordered on it at destroy
-  vie::FftPlan plan2n;       // length-2n line DFT (Bluestein's algorithm when 2n is not smooth)
-  double2* tw64 = nullptr;   // its line table: exp(-2 pi i j / Q), j < Q, then the Bluestein tables
+  // Convolution grid: M = 2 nk points per axis.  nk = n when 2n factors into
+  // the codelet radices 2, 3, 5, 7, 11, else the smallest such nk > n: a
+  // circular convolution of length M >= 2n - 1 equals the zero-padded linear
+  // one on the n^3 output nodes, so the apply never needs Bluestein lines.
+  int nk = 0;
+  vie::FftPlan planM;        // length-M line DFT (direct)
+  double2* tw64 = nullptr;   // its line table: exp(-2 pi i j / M), j < M
   float2* tw32 = nullptr;
   double2* He64 = nullptr;   // [6][n^3] symmetric H_eps (xx yy zz xy xz yz)
   float2* He32 = nullptr;
@@ -138,7 +143,9 @@ vie_status build_df(vie_problem* P, cudaStream_t st);
 // (u = the convolution); otherwise out = u.
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
                      bool with_identity, cudaStream_t st);
-size_t apply_workspace_bytes(int n, int c, int nrhs, int prec);
+size_t apply_workspace_bytes(int n, int nk, int c, int nrhs, int prec);
+// Kernel half-size nk of an n-point grid (the convolution grid is 2 nk).
+int conv_half(int n);
 // Grow the padded-intermediate workspace for an apply of K at this precision and
 // nrhs (stream-ordered on st); afterwards run_apply does not allocate.
 vie_status ensure_apply_workspace(vie_problem* P, const KernelSet& K, int prec, int nrhs, cudaStream_t st);

@@ -1,17 +1,18 @@
-"""GPU parity at grid sizes whose line lengths have a prime factor above 11.
+"""GPU parity at grid sizes with a prime factor above 11.
 
-For n = 13, 17, 26, 34 the convolution lines 2n (26, 34, 52, 68) and the set-up
-lines 3n (39, 51, 78, 102) do not factor into the codelet radices 2, 3, 5, 7,
-11: every transform runs Bluestein's chirp-z algorithm (a length-2n DFT as a
-circular convolution of padded smooth length Q >= 4n - 1), in the apply
-kernels and in the set-up's kernel transforms alike.  The oracle transforms
-these lengths with numpy's FFT.
+For n = 13, 17, 26, 34 the set-up lines 3n (39, 51, 78, 102) do not factor
+into the codelet radices 2, 3, 5, 7, 11: the set-up's kernel transforms run
+Bluestein's chirp-z algorithm (a length-3n DFT as a circular convolution of
+padded smooth length Q >= 6n - 1).  2n (26, 34, 52, 68) does not factor
+either, so the apply runs on the padded convolution grid M = 2 nk (28, 36,
+54, 70), nk the smallest smooth number >= n: a circular convolution of length
+M >= 2n - 1 is the same zero-padded linear convolution on the n^3 nodes.  The
+oracle transforms these lengths with numpy's FFT on the 2n grid.
 
 Tolerances are those of the other parity tests: 1e-12 for FP64 and
-double-word applies and the scattered field (Bluestein's algorithm adds two
-length-Q transforms and three complex multiplications per line, a few more
-rounding steps of size eps_64), 2e-5 for FP32 applies, 1e-8 for solves
-stopped at a relative residual of 1e-10.
+double-word applies and the scattered field (a different grid length changes
+only the rounding order), 2e-5 for FP32 applies, 1e-8 for solves stopped at a
+relative residual of 1e-10.
 """
 import numpy as np
 import pytest
