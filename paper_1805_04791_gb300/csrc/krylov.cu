@@ -238,6 +238,15 @@ __global__ void k_scale(TD* __restrict__ dst, const TS* __restrict__ src, const 
 }
 
 // r = b - r
+// r -= y (y the FP32 apply of a refinement correction)
+__global__ void k_rminus32(double2* __restrict__ r, const float2* __restrict__ y, long long L) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = y[i];
+    r[i].x -= (double)v.x;
+    r[i].y -= (double)v.y;
+  }
+}
+
 __global__ void k_bminus(double2* __restrict__ r, const double2* __restrict__ b, long long L) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x)
     r[e] = b[e] - r[e];
@@ -275,6 +284,7 @@ struct ArnState {
   double stop;   // absolute stopping threshold of the cycle
   double wn2;    // |w|^2 of the current step before projection
   double beta;   // initial residual norm of the cycle
+  double ynorm;  // |y| of the cycle's least-squares solution: the norm of its correction
 };
 
 __host__ __device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
@@ -704,13 +714,20 @@ __global__ void k_arn_solve(ArnLayout A, int nb) {
     const double dd = dnorm2(d);
     y[i] = dscale(1.0 / dd, cmul(acc, dconj(d)));
   }
+  // the correction sum_i y_i v_i has norm |y| (orthonormal v_i, to the basis
+  // precision's orthogonality)
+  double yn = 0.0;
+  for (int i = 0; i < k; ++i) yn += dnorm2(y[i]);
+  A.st[r].ynorm = sqrt(yn);
   for (int i = 0; i < k; ++i) y[i] = dscale(sc[i], y[i]);
 }
 
-// x[r] += sum_{i < steps[r]} coef[r][i] W_i[r]  (x FP64, products in TB's precision).  grid = (blocks, nb).
+// x[r] += d[r] = sum_{i < steps[r]} coef[r][i] W_i[r]  (x FP64, products in TB's
+// precision); d is also stored to dout[r] when dout is given (a basis slot the
+// sum does not read).  grid = (blocks, nb).
 template <typename TB>
 __global__ void k_arn_update(double2* __restrict__ x, const TB* __restrict__ V, long long ldi, ArnLayout A,
-                             long long L) {
+                             long long L, TB* __restrict__ dout) {
   typedef typename Acc<TB>::T AT;
   __shared__ typename Acc<TB>::V cs[256];
   const int r = blockIdx.y, m = A.m;
@@ -720,7 +737,12 @@ __global__ void k_arn_update(double2* __restrict__ x, const TB* __restrict__ V, 
     cs[i].y = (AT)A.coef[(long long)r * m + i].y;
   }
   __syncthreads();
-  if (k == 0) return;
+  if (k == 0) {  // no correction: d = 0
+    if (dout)
+      for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x)
+        dout[(long long)r * L + e] = TB{};
+    return;
+  }
   double2* xr = x + (long long)r * L;
   const TB* Vr = V + (long long)r * L;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L; e += (long long)gridDim.x * blockDim.x) {
@@ -732,6 +754,12 @@ __global__ void k_arn_update(double2* __restrict__ x, const TB* __restrict__ V, 
     }
     xr[e].x += (double)ax;
     xr[e].y += (double)ay;
+    if (dout) {
+      TB d;
+      d.x = ax;
+      d.y = ay;
+      dout[(long long)r * L + e] = d;
+    }
   }
 }
 
@@ -793,7 +821,7 @@ static vie_status ensure_mirror(vie_problem* P, int nb) {
 template <typename TB>
 static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double>& beta, double2* x,
                               const std::vector<double>& stop_abs, std::vector<int>& steps, int* applies,
-                              cudaStream_t st) {
+                              cudaStream_t st, TB* dout = nullptr, std::vector<double>* dnorm = nullptr) {
   const long long L = g.L;
   const int nb = g.nb, m = g.m;
   const long long ldi = (long long)nb * L;
@@ -957,7 +985,7 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
   // back substitution and x += V y on the device; the final state to the host
   k_arn_solve<<<(nb + 63) / 64, 64, 0, st>>>(A, nb);
   VIE_CK(cudaGetLastError());
-  k_arn_update<TB><<<ewg, 256, 0, st>>>(x, V, ldi, A, L);
+  k_arn_update<TB><<<ewg, 256, 0, st>>>(x, V, ldi, A, L, dout);
   VIE_CK(cudaGetLastError());
   std::vector<ArnState> fin(nb);
   VIE_CK(cudaMemcpyAsync(fin.data(), A.st, sizeof(ArnState) * nb, cudaMemcpyDeviceToHost, st));
@@ -969,6 +997,10 @@ static vie_status gmres_cycle(vie_problem* P, Group& g, const std::vector<double
     }
     steps[r] = fin[r].steps;
     *applies += fin[r].steps;
+  }
+  if (dnorm) {
+    dnorm->resize(nb);
+    for (int r = 0; r < nb; ++r) (*dnorm)[r] = fin[r].steps > 0 ? fin[r].ynorm : 0.0;
   }
   return VIE_OK;
 }
@@ -1265,6 +1297,20 @@ static bool residual_fp64() {
   const char* e = getenv("VIE_RESIDUAL_FP64");
   return e && e[0] == '1';
 }
+static bool residual_update_allowed() {
+  const char* e = getenv("VIE_RESIDUAL_UPDATE");
+  return !(e && e[0] == '0');
+}
+
+// Bound on |A_32 d - A d| for the FP32 apply of d: the forward and inverse
+// transforms of the convolution, log2(M^3) butterfly levels each, with a few
+// roundings of u = 2^-24 per level (a generous 8 u log2(M^3) in all), scaled by
+// the bound ||A|| <= opnorm of the set-up; plus the rounding of d to FP32.
+static double fp32_apply_error(const vie_problem* P, double dn) {
+  const double u = 5.9604644775390625e-8;
+  const double M = 2.0 * P->nk;
+  return (8.0 * u * 3.0 * std::log2(M) + u) * P->opnorm * dn * 1.01;
+}
 
 vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_opts* opt, vie_solve_info* info,
                      cudaStream_t st) {
@@ -1323,12 +1369,30 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
     }
     std::vector<char> conv(nb, 0);
     int total_inner = 0;
+    // mixed: after a small correction d the residual is updated as r -= A_32 d
+    // (an FP32 apply) instead of recomputed as b - A x (a double-word apply),
+    // when the bound on the FP32 apply's error is at most half the tolerance;
+    // err holds the accumulated bound, and convergence is judged on |r| + err.
+    std::vector<double> err(nb, 0.0), dn(nb, 0.0);
+    bool update_next = false;
     const int max_outer = mixed ? opt->max_outer : std::max(1, opt->max_outer);
     for (int outer = 0; outer <= max_outer; ++outer) {
       // FP64 residuals r = b - A x (r = b for zero initial guesses)
       if (outer == 0 && x_zero) {
         VIE_CK(cudaMemcpyAsync(g.r, b, sizeof(double2) * nb * L, cudaMemcpyDeviceToDevice, st));
         beta = nbv;
+      } else if (update_next) {
+        // d is in basis slot m (FP32); its apply goes to slot 0
+        float2* Vb = (float2*)g.V;
+        const long long ldi = (long long)nb * L;
+        s = run_apply(P, P->kapply, Vb + (long long)m * ldi, Vb, VIE_FP32, nb, true, st);
+        if (s != VIE_OK) return s;
+        inf.applies_fp32 += nb;
+        k_rminus32<<<ew_blocks(L * nb), 256, 0, st>>>(g.r, Vb, L * nb);
+        VIE_CK(cudaGetLastError());
+        s = norms_host(g.r, g, beta, st);
+        if (s != VIE_OK) return s;
+        for (int r = 0; r < nb; ++r) err[r] += fp32_apply_error(P, dn[r]);
       } else {
         // mixed: the residual in double-word arithmetic (FP64 accuracy, FP32
         // pipes); VIE_RESIDUAL_FP64=1 takes the native FP64 apply instead
@@ -1339,6 +1403,7 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
         VIE_CK(cudaGetLastError());
         s = norms_host(g.r, g, beta, st);
         if (s != VIE_OK) return s;
+        std::fill(err.begin(), err.end(), 0.0);
       }
       bool all = true;
       std::vector<double> stop(nb), bx(nb);
@@ -1347,7 +1412,7 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
           set_error("non-finite residual");
           return VIE_ENAN;
         }
-        rel[r] = nbv[r] > 0 ? beta[r] / nbv[r] : 0.0;
+        rel[r] = nbv[r] > 0 ? (beta[r] + err[r]) / nbv[r] : 0.0;
         conv[r] = rel[r] <= opt->tol;
         if (!conv[r]) all = false;
         // converged members ride along with zero vectors
@@ -1361,8 +1426,15 @@ vie_status run_solve(vie_problem* P, const void* rhs, void* Jv, const vie_solve_
       int ap = 0;
       g.m = std::min(m, opt->max_inner - total_inner);
       if (mixed) {
-        s = gmres_cycle<float2>(P, g, bx, x, stop, steps, &ap, st);
+        const bool upd = residual_update_allowed() && !residual_fp64();
+        // slot m: the last basis vector, which the update of x does not read
+        float2* dslot = upd ? (float2*)g.V + (long long)m * nb * L : nullptr;
+        s = gmres_cycle<float2>(P, g, bx, x, stop, steps, &ap, st, dslot, upd ? &dn : nullptr);
         inf.applies_fp32 += ap;
+        // update the next residual if every member's bound stays within half the tolerance
+        update_next = upd && s == VIE_OK;
+        for (int r = 0; r < nb && update_next; ++r)
+          if (err[r] + fp32_apply_error(P, dn[r]) > 0.5 * opt->tol * nbv[r]) update_next = false;
       } else {
         s = gmres_cycle<double2>(P, g, bx, x, stop, steps, &ap, st);
         inf.applies_fp64 += ap;

@@ -10,6 +10,7 @@
 //    grid and stored as octants (the kernels are even or odd in each axis).
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -456,6 +457,53 @@ static const unsigned kDmask = (1u << SYM_DX) | (1u << SYM_DY) | (1u << SYM_DZ);
 // Kernel sets: `which` 0 = operator apply, 1 = scattered field.
 static vie_status combine_sets(vie_problem* P, int which, cudaStream_t st);
 
+// ------------------------------------------------ operator norm bound
+__device__ __forceinline__ double dnorm2c(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// max over points of the Frobenius norm of a symmetric 3x3 tensor field stored
+// as 6 arrays (xx yy zz xy xz yz) of stride S, with 3 more arrays (a curl
+// symbol p: the 6x6 Maxwell kernel [[Q, p x], [-p x, Q]]) when np == 3, into
+// *out as the bit pattern of a non-negative double (ordered like the double).
+__global__ void k_fro_max(const double2* __restrict__ a, long long S, int np, unsigned long long* out) {
+  double mx = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+    double f = 0.0;
+    for (int e = 0; e < 6; ++e) f += (e < 3 ? 1.0 : 2.0) * dnorm2c(a[e * S + i]);
+    if (np == 3) {
+      double p = 0.0;
+      for (int e = 6; e < 9; ++e) p += dnorm2c(a[e * S + i]);
+      f = 2.0 * f + 4.0 * p;
+    }
+    mx = fmax(mx, f);
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sqrt(mx)));
+}
+
+// Upper bound of ||A||_2 = ||I + H conv||_2 <= 1 + max ||H||_F max_k ||K^(k)||_F with
+// the kernel's eigenvalues M^3 K_stored (the 1/M^3 of the inverse DFT is folded
+// into the stored octants).  Used to bound the error of an FP32 apply.
+static vie_status op_norm_bound(vie_problem* P, cudaStream_t st) {
+  unsigned long long* d = nullptr;
+  VIE_CK(dalloc((void**)&d, 3 * sizeof(unsigned long long), st));
+  VIE_CK(cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), st));
+  const long long O = P->nk + 1, O3 = O * O * O, N = (long long)P->n * P->n * P->n;
+  const int np = P->kapply.mode == KM_MAXWELL6 ? 3 : 0;
+  k_fro_max<<<152 * 4, 256, 0, st>>>(P->kapply.oct64, O3, np, d);
+  k_fro_max<<<152 * 4, 256, 0, st>>>(P->He64, N, 0, d + 1);
+  if (P->Hm64) k_fro_max<<<152 * 4, 256, 0, st>>>(P->Hm64, N, 0, d + 2);
+  VIE_CK(cudaGetLastError());
+  unsigned long long h[3];
+  VIE_CK(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+  VIE_CK(cudaStreamSynchronize(st));
+  dfree(d, st);
+  double v[3];
+  for (int i = 0; i < 3; ++i) memcpy(&v[i], &h[i], sizeof(double));
+  const double M = 2.0 * P->nk;
+  P->opnorm = 1.0 + std::max(v[1], v[2]) * v[0] * M * M * M;
+  return VIE_OK;
+}
+
 vie_status build_kernels(vie_problem* P, cudaStream_t st) {
   // the operator needs -k_a k_b (and, for Maxwell, 1; with mu also the curl
   // symbols i k_a); the symbols only the scattered field needs are built on
@@ -464,7 +512,9 @@ vie_status build_kernels(vie_problem* P, cudaStream_t st) {
   if (P->kind == VIE_MAXWELL) mask |= (1u << SYM_1) | (P->has_mu ? kDmask : 0u);
   vie_status s = compute_symbols(P, mask, st);
   if (s != VIE_OK) return s;
-  return combine_sets(P, 0, st);
+  s = combine_sets(P, 0, st);
+  if (s != VIE_OK) return s;
+  return op_norm_bound(P, st);
 }
 
 vie_status build_eval_kernels(vie_problem* P, cudaStream_t st) {

@@ -96,6 +96,7 @@ struct vie_problem {
   int p3_variant[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // tuned z-pass variant per (precision, mode)
   int* dflag = nullptr;      // device error flag (NaN, bad input)
   double t_precompute = 0;   // wall seconds of the set-up in vie_problem_create
+  double opnorm = 0;         // upper bound of ||A||_2 of the operator (set-up)
   // device-resident GMRES: pinned host copies of the per-member Arnoldi state
   // (one slot per step in flight) and the events that mark each copy complete
   void* arn_host = nullptr;

@@ -148,3 +148,32 @@ def test_graph_replayed_steps_equal_direct_launches(vie, monkeypatch, kind, n, m
         assert np.array_equal(a, g)
     op = operators.OracleProblem.from_problem(p)
     assert rel(outs["1"][-1], _oracle_solution(op, p, 0)) <= 1e-8
+
+
+@pytest.mark.parametrize("kind,n,wl", [("helmholtz", 64, 4.0), ("laplace", 32, 0.0)])
+def test_fp32_updated_residual_is_certified(vie, monkeypatch, kind, n, wl):
+    """At tol = 1e-8 the residual after a small refinement correction d is updated
+    as r -= A_32 d (FP32 apply) when the bound on that apply's error is within half
+    the tolerance; the reported residual includes the bound, so the native FP64
+    residual of the answer is below it.  With VIE_RESIDUAL_UPDATE=0 every residual
+    is a double-word apply; both answers agree with the oracle."""
+    import torch
+
+    p = _problem(kind, n, wl, False, seed=8)
+    op = operators.OracleProblem.from_problem(p)
+    Jo = _oracle_solution(op, p, 0)
+    res = {}
+    for upd in ("1", "0"):
+        monkeypatch.setenv("VIE_RESIDUAL_UPDATE", upd)
+        P = vie.Problem(kind, n, p.lo, p.hi, p.omega, eps_dev(p), mu_dev(p))
+        b = torch.empty((P.ncomp, n, n, n), dtype=torch.complex128, device="cuda:0")
+        P.rhs(p.directions[0], None, 1, b)
+        J = torch.zeros_like(b)
+        st, info = P.solve(b, J, tol=1e-8, restart=50, mode=vie.VIE_SOLVE_MIXED, check_fp64=True)
+        assert st == vie.VIE_OK and info.rel_residual <= 1e-8
+        assert 0.0 <= info.rel_residual_fp64 <= info.rel_residual * 1.0001 + 1e-14
+        assert rel(J.cpu().numpy(), Jo) <= 1e-6
+        res[upd] = info
+        P.close()
+    # the updated path replaces double-word residual applies by FP32 ones
+    assert res["1"].applies_fp64 < res["0"].applies_fp64
