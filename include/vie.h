@@ -54,6 +54,9 @@
  *                       FP64 apply instead of the double-word one.
  * - VIE_SETUP_FP64=1    the set-up's kernel-transform FFTs run in native FP64
  *                       instead of double-word arithmetic.
+ * - VIE_RESIDUAL_UPDATE=0 mixed solves recompute every refinement residual
+ *                       as b - A x (double-word apply) instead of updating it
+ *                       with an FP32 apply of a small correction.
  * - VIE_GRAPHS=0        single right-hand-side GMRES steps are launched kernel by
  *                       kernel instead of being replayed from captured CUDA graphs.
  */
@@ -120,7 +123,11 @@ typedef struct {
                              mode's refinement residuals (VIE_RESIDUAL_FP64=1: native) */
   double rel_residual;    /* max over right-hand sides of the final relative residual, as the
                              solver computed it: native FP64 (FP64, Bi-CGStab) or double-word
-                             (mixed; relative error of that apply near 1e-13) */
+                             (mixed; relative error of that apply near 1e-13).  A mixed
+                             residual updated after a small correction d as r - A_32 d (FP32
+                             apply; taken when the bound 8 u log2(M^3) ||A|| ||d||, u = 2^-24,
+                             is within half the tolerance) is reported as |r| plus that bound:
+                             an upper bound of the true residual */
   double t_solve;         /* wall seconds spent in vie_solve */
   double t_precompute;    /* wall seconds vie_problem_create spent on this handle's set-up
                              (medium tensors and kernel transforms, Sec. 5) */
