@@ -240,9 +240,15 @@ __global__ void k_p5(const typename CT<T>::V* __restrict__ A, const typename IOT
         const typename IOT<T>::E* xi = xin + ((long long)b * cout + 3 * blk) * N + pt;
         typename IOT<T>::E* yo = y + ((long long)b * cout + 3 * blk) * N + pt;
         const V a0 = u[3 * blk], a1 = u[3 * blk + 1], a2 = u[3 * blk + 2];
-        yo[0] = from_v<T>(to_v<T>(xi[0]) + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
-        yo[N] = from_v<T>(to_v<T>(xi[N]) + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
-        yo[2 * N] = from_v<T>(to_v<T>(xi[2 * N]) + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
+        if (with_identity == 1) {
+          yo[0] = from_v<T>(to_v<T>(xi[0]) + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
+          yo[N] = from_v<T>(to_v<T>(xi[N]) + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
+          yo[2 * N] = from_v<T>(to_v<T>(xi[2 * N]) + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
+        } else {  // 2: H u alone
+          yo[0] = from_v<T>(cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
+          yo[N] = from_v<T>(cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
+          yo[2 * N] = from_v<T>(cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
+        }
       }
     } else {
       for (int c = 0; c < cout; ++c) y[((long long)b * cout + c) * N + pt] = from_v<T>(u[c]);
@@ -312,7 +318,7 @@ struct FastSel {
 // per line: 2n when the convolution grid is 2n, else 0 (no fast kernels).
 static int fast_grid(const vie_problem* P) { return P->nk == P->n ? 2 * P->n : 0; }
 
-static FastSel fast_select(int M, int mode, bool with_identity) {
+static FastSel fast_select(int M, int mode, int with_identity) {
   FastSel f;
   if (M != 64 && M != 96 && M != 128 && M != 192 && M != 256 && M != 384 && M != 512) return f;
   if (getenv("VIE_GENERIC_FFT")) return f;
@@ -350,7 +356,7 @@ bool p3_schedule_ready(vie_problem* P, const KernelSet& K, int prec) {
 
 
 static vie_status fast_dispatch(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                                bool with_identity, void* A, void* B, int C, int prec, cudaStream_t st,
+                                int with_identity, void* A, void* B, int C, int prec, cudaStream_t st,
                                 bool* used = nullptr) {
   if (prec == VIE_DF64) {
     bool u = true;
@@ -400,7 +406,7 @@ vie_status ensure_apply_workspace(vie_problem* P, const KernelSet& K, int prec, 
 
 template <typename T>
 static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                              bool with_identity, cudaStream_t st) {
+                              int with_identity, cudaStream_t st) {
   typedef typename CT<T>::V V;
   const int n = P->n, M = 2 * P->nk;
   const int cin = cin_of(K.mode), cout = cout_of(K.mode);
@@ -534,7 +540,7 @@ static vie_status run_apply_t(vie_problem* P, const KernelSet& K, const void* in
     const V* Hm = P->has_mu ? Prec<T>::Hm(P) : nullptr;
     k_p5<T><<<grid, block_for(pl, cout * nr), smem, st>>>(A, (const typename IOT<T>::E*)in, (typename IOT<T>::E*)out, n, pl, tw, nr, C,
                                      cout, He, Hm,
-                                     with_identity ? 1 : 0);
+                                     with_identity);
     VIE_CK(cudaGetLastError());
     if (rec) VIE_CK(cudaEventRecord(ev[5], st));
   }
@@ -568,7 +574,7 @@ vie_status tune_apply(vie_problem* P, const KernelSet& K, int prec, int* variant
 }
 
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
-                     bool with_identity, cudaStream_t st) {
+                     int with_identity, cudaStream_t st) {
   if (prec == VIE_FP64) return run_apply_t<double>(P, K, in, out, nrhs, with_identity, st);
   if (prec == VIE_DF64) {
     // double-word tables exist for the operator kernels only

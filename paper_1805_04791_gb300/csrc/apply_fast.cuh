@@ -1018,8 +1018,8 @@ f_p3s(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
   }
 }
 
-// x-lines of all components: inverse, keep x < n, epilogue y = x + H u (or
-// y = u).  CO = 3 (one H block) or 6 ([J; M] with H_eps and H_mu, or [E; H]).
+// x-lines of all components: inverse, keep x < n, epilogue y = x + H u
+// (with_identity 1), y = H u (2: the operator minus the identity) or y = u (0).  CO = 3 (one H block) or 6 ([J; M] with H_eps and H_mu, or [E; H]).
 template <typename T, int R1, int R2, int CO>
 __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict__ A,
                                             const typename IOT<T>::E* __restrict__ xin, typename IOT<T>::E* __restrict__ y,
@@ -1082,9 +1082,15 @@ __global__ void __launch_bounds__(256) f_p5(const typename CT<T>::V* __restrict_
         const typename IOT<T>::E* xi = xin + ((long long)b * CO + 3 * blk) * N + pt;
         typename IOT<T>::E* yo = y + ((long long)b * CO + 3 * blk) * N + pt;
         const V a0 = uo[3 * blk][n1], a1 = uo[3 * blk + 1][n1], a2 = uo[3 * blk + 2][n1];
-        yo[0] = from_v<T>(to_v<T>(xi[0]) + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
-        yo[N] = from_v<T>(to_v<T>(xi[N]) + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
-        yo[2 * N] = from_v<T>(to_v<T>(xi[2 * N]) + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
+        if (with_identity == 1) {
+          yo[0] = from_v<T>(to_v<T>(xi[0]) + cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
+          yo[N] = from_v<T>(to_v<T>(xi[N]) + cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
+          yo[2 * N] = from_v<T>(to_v<T>(xi[2 * N]) + cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
+        } else {  // 2: H u alone
+          yo[0] = from_v<T>(cmul(hxx, a0) + cmul(hxy, a1) + cmul(hxz, a2));
+          yo[N] = from_v<T>(cmul(hxy, a0) + cmul(hyy, a1) + cmul(hyz, a2));
+          yo[2 * N] = from_v<T>(cmul(hxz, a0) + cmul(hyz, a1) + cmul(hzz, a2));
+        }
       }
     } else {
 #pragma unroll
@@ -1286,15 +1292,15 @@ struct FastPath {
       default: return p3_mode<KM_MAXWELL6>(variant, B, n, C, K, nrhs, tw, done, st);
     }
   }
-  static vie_status p5(const V* A, const E* xin, E* y, int n, int C, int cout, const V* He, const V* Hm, bool wid,
+  static vie_status p5(const V* A, const E* xin, E* y, int n, int C, int cout, const V* He, const V* Hm, int wid,
                        int nrhs, const V* tw, cudaStream_t st) {
     const dim3 grid((n * n + L - 1) / L, nrhs);
     if (cout <= 3) {
       VIE_CK(allow_smem(f_p5<T, R1, R2, 3>));
-      f_p5<T, R1, R2, 3><<<grid, 256, smem(), st>>>(A, xin, y, n, C, cout, He, Hm, wid ? 1 : 0, tw);
+      f_p5<T, R1, R2, 3><<<grid, 256, smem(), st>>>(A, xin, y, n, C, cout, He, Hm, wid, tw);
     } else {
       VIE_CK(allow_smem(f_p5<T, R1, R2, 6>));
-      f_p5<T, R1, R2, 6><<<grid, 256, smem(), st>>>(A, xin, y, n, C, cout, He, Hm, wid ? 1 : 0, tw);
+      f_p5<T, R1, R2, 6><<<grid, 256, smem(), st>>>(A, xin, y, n, C, cout, He, Hm, wid, tw);
     }
     VIE_CK(cudaGetLastError());
     return VIE_OK;
@@ -1303,7 +1309,7 @@ struct FastPath {
 
 template <typename T, int R1, int R2>
 vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                            bool with_identity, typename CT<T>::V* A, typename CT<T>::V* B, int C, cudaStream_t st) {
+                            int with_identity, typename CT<T>::V* A, typename CT<T>::V* B, int C, cudaStream_t st) {
   typedef FastPath<T, R1, R2> FP;
   typedef typename CT<T>::V V;
   const int n = P->n;
@@ -1409,7 +1415,7 @@ vie_status tune_p3(vie_problem* P, const KernelSet& K, typename CT<T>::V* B, int
 // *used = false if this (pass, mode) has no double-word fast kernel.
 template <int R1, int R2>
 vie_status fast_pass_dw(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                        bool with_identity, cdf* A, cdf* B, int C, cudaStream_t st, bool* used) {
+                        int with_identity, cdf* A, cdf* B, int C, cudaStream_t st, bool* used) {
   typedef FastPath<df, R1, R2> FP;
   const int n = P->n;
   const cdf* tw = Prec<df>::tw(P);
@@ -1437,20 +1443,20 @@ vie_status fast_pass_dw(int pass, vie_problem* P, const KernelSet& K, const void
   }
 }
 vie_status fast_pass_dw_256(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                            bool wid, void* A, void* B, int C, cudaStream_t st, bool* used);
+                            int wid, void* A, void* B, int C, cudaStream_t st, bool* used);
 
 // Per-size entry points (one translation unit each).
 #define VIE_FAST_SIZES(X) X(64, 8, 8) X(96, 12, 8) X(128, 16, 8) X(192, 24, 8) X(256, 16, 16) X(384, 24, 16) X(512, 32, 16)
 
 #define VIE_FAST_DECL(MM, RA, RB)                                                                                   \
   vie_status fast_pass_##MM(bool f64, int pass, vie_problem* P, const KernelSet& K, const void* in, void* out,       \
-                            int nrhs, bool wid, void* A, void* B, int C, cudaStream_t st);                         \
+                            int nrhs, int wid, void* A, void* B, int C, cudaStream_t st);                         \
   vie_status tune_p3_##MM(bool f64, vie_problem* P, const KernelSet& K, void* B, int C, cudaStream_t st, int* best);
 VIE_FAST_SIZES(VIE_FAST_DECL)
 
 #define VIE_FAST_DEFINE(MM, RA, RB)                                                                                 \
   vie_status fast_pass_##MM(bool f64, int pass, vie_problem* P, const KernelSet& K, const void* in, void* out,       \
-                            int nrhs, bool wid, void* A, void* B, int C, cudaStream_t st) {                        \
+                            int nrhs, int wid, void* A, void* B, int C, cudaStream_t st) {                        \
     return f64 ? fast_pass<double, RA, RB>(pass, P, K, in, out, nrhs, wid, (double2*)A, (double2*)B, C, st)         \
                : fast_pass<float, RA, RB>(pass, P, K, in, out, nrhs, wid, (float2*)A, (float2*)B, C, st);           \
   }                                                                                                                \

@@ -3,7 +3,7 @@
 
 namespace vie {
 vie_status fast_pass_dw_256(int pass, vie_problem* P, const KernelSet& K, const void* in, void* out, int nrhs,
-                            bool wid, void* A, void* B, int C, cudaStream_t st, bool* used) {
+                            int wid, void* A, void* B, int C, cudaStream_t st, bool* used) {
   return fast_pass_dw<16, 16>(pass, P, K, in, out, nrhs, wid, (cdf*)A, (cdf*)B, C, st, used);
 }
 }  // namespace vie

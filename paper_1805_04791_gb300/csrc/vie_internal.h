@@ -140,10 +140,11 @@ vie_status build_df(vie_problem* P, cudaStream_t st);
 
 // apply.cu
 // Convolution pipeline: out = epilogue(K * pad(in)).  prec: vie_precision.
-// in/out layout [nrhs][c][n][n][n] complex.  If with_identity, out = in + H u
-// (u = the convolution); otherwise out = u.
+// in/out layout [nrhs][c][n][n][n] complex.  with_identity 1: out = in + H u;
+// 2: out = H u (the operator minus the identity); 0: out = u (u = the
+// convolution).
 vie_status run_apply(vie_problem* P, const KernelSet& K, const void* in, void* out, int prec, int nrhs,
-                     bool with_identity, cudaStream_t st);
+                     int with_identity, cudaStream_t st);
 size_t apply_workspace_bytes(int n, int nk, int c, int nrhs, int prec);
 // Kernel half-size nk of an n-point grid (the convolution grid is 2 nk).
 int conv_half(int n);
