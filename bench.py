@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df64"],
                     help="precision of the --case apply run")
+    ap.add_argument("--kind", default="helmholtz", choices=["helmholtz", "maxwell"],
+                    help="operator of the --case apply run (maxwell: with mu, 10 wavelengths)")
     return ap.parse_args()
 
 
@@ -136,6 +138,9 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def count(self):
+        return len(self.lines)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -172,16 +177,19 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(n, c, esz):
+def algorithmic_bytes(n, c, esz, narr=6, nh=6):
     """Bytes each pass must move (values per grid point x N x element size).
 
     P1 reads c N, writes 2c N; P2 reads 2c N, writes 4c N; P3 reads and writes
-    4c N plus the 6 kernel octants ((n+1)^3 each); P4 reads 4c N, writes 2c N;
-    P5 reads 2c N + x (c N) + H (6 N), writes c N.
+    4c N plus the narr kernel octants ((n+1)^3 each: 6 for the 3x3 symmetric
+    kernel set, 9 for Maxwell's); P4 reads 4c N, writes 2c N; P5 reads 2c N + x
+    (c N) + the nh medium-tensor values per point (6 for H_eps, 12 with H_mu),
+    writes c N.
     """
     N = n ** 3
     O3 = (n + 1) ** 3
-    return [3 * c * N * esz, 6 * c * N * esz, (8 * c * N + 6 * O3) * esz, 6 * c * N * esz, (4 * c * N + 6 * N) * esz]
+    return [3 * c * N * esz, 6 * c * N * esz, (8 * c * N + narr * O3) * esz, 6 * c * N * esz,
+            (4 * c * N + nh * N) * esz]
 
 
 def pct(v, q):
@@ -399,12 +407,46 @@ def leg_maxwell256(args, dev):
     P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, eps, mu)
     t_setup = time.perf_counter() - t0
     del eps, mu
-    P.tune(vie.VIE_FP32)
+    v32 = P.tune(vie.VIE_FP32)
     P.tune(vie.VIE_FP64)
+    out = {"workload": f"maxwell_mu_bump_{n}", "setup_s": t_setup}
+    # FP32 apply: CUDA events over 10 applies (x and y are 805 MB each, > L2),
+    # then the same applies with per-pass events
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    x32 = torch.randn((6, n, n, n), dtype=torch.complex64, device=dev, generator=g)
+    y32 = torch.empty_like(x32)
+    for _ in range(2):
+        P.apply(x32, y32, vie.VIE_FP32)
+    torch.cuda.synchronize()
+    reps = 10
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        P.apply(x32, y32, vie.VIE_FP32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / reps
+    vie.vie_profile_begin(P.handle, reps)
+    for _ in range(reps):
+        P.apply(x32, y32, vie.VIE_FP32)
+    pass_ms, cnt = vie.vie_profile_end(P.handle)
+    del x32, y32
+    peak, peak_src = load_peaks()
+    names = ["P1_fwd_x", "P2_fwd_y", "P3_z_kernel_z", "P4_inv_y", "P5_inv_x_epilogue"]
+    ab = algorithmic_bytes(n, 6, 8, narr=9, nh=12)
+    passes = {}
+    for k in range(5):
+        ms = pass_ms[k] / max(cnt, 1)
+        passes[names[k]] = {"avg_ms": ms, "alg_bytes": ab[k],
+                            "gbs": ab[k] / (ms / 1000.0) / 1e9 if ms > 0 else None}
+    out["fp32_apply"] = {"ms": apply_ms, "applies_per_s": 1000.0 / apply_ms, "p3_variant": v32,
+                         "alg_bytes": sum(ab), "frac_of_peak": sum(ab) / (apply_ms / 1000.0) / 1e9 / peak,
+                         "peak_gbs": peak, "peak_source": peak_src, "passes": passes}
     b = torch.empty((6, n, n, n), dtype=torch.complex128, device=dev)
     P.rhs(p.directions[0], p.polarisations[0], 1, b)
     J = torch.zeros_like(b)
-    out = {"workload": f"maxwell_mu_bump_{n}", "setup_s": t_setup}
     for name, mode in (("mixed", vie.VIE_SOLVE_MIXED), ("fp64", vie.VIE_SOLVE_FP64)):
         J.zero_()
         torch.cuda.synchronize()
@@ -704,12 +746,21 @@ def run_ours(args):
         P.apply(xs[i % N_BUFS], ys[i % N_BUFS], prec)
 
     # ---------------- FP32 apply (the metric's step)
-    for i in range(max(3, args.warmup)):
-        step(i)
-    torch.cuda.synchronize()
-    barrier()
+    # nvidia-smi takes a few hundred ms to report its first sample, longer than
+    # a short timed region: the sampler starts before the warm-up, and the
+    # warm-up continues (untimed, counted in warmup_run) until two samples
+    # under load have arrived, so the reported clocks are those of the loaded
+    # GPU just before and during the timed steps.
     clocks = ClockSampler(local)
     clocks.start()
+    n_warm, t_warm = 0, time.perf_counter()
+    while n_warm < max(3, args.warmup) or (clocks.count() < 2 and time.perf_counter() - t_warm < 3.0):
+        step(n_warm)
+        n_warm += 1
+        if n_warm % 8 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -868,7 +919,7 @@ def run_ours(args):
         line = {
             "metric": METRIC,
             "value": applies_per_s, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "warmup": max(3, args.warmup), "warmup_run": n_warm, "ms_per_step": total_ms / args.steps,
             "p50_ms": pct(per, 50), "p99_ms": pct(per, 99),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
@@ -915,11 +966,16 @@ def run_case(args):
 
     dev = torch.device("cuda:0")
     n = args.n
-    p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
-    P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev))
+    if args.kind == "maxwell":  # Maxwell with mu, 10 wavelengths (the 256^3 workload's medium)
+        p = vi.maxwell_problem(n=n, wavelengths=10.0, with_mu=True, seed=0)
+        P = vie.Problem("maxwell", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev),
+                        torch.from_numpy(p.mu.reshape(9, -1).copy()).to(dev))
+    else:
+        p = vi.helmholtz_problem(n=n, wavelengths=4.0, seed=0)
+        P = vie.Problem("helmholtz", n, p.lo, p.hi, p.omega, torch.from_numpy(p.eps.reshape(9, -1).copy()).to(dev))
     prec = {"fp32": vie.VIE_FP32, "fp64": vie.VIE_FP64, "df64": vie.VIE_DF64}[args.prec]
     dt = torch.complex64 if args.prec == "fp32" else torch.complex128
-    x = torch.randn((3, n, n, n), dtype=dt, device=dev)
+    x = torch.randn((P.ncomp, n, n, n), dtype=dt, device=dev)
     y = torch.empty_like(x)
     for _ in range(args.reps):
         P.apply(x, y, prec)

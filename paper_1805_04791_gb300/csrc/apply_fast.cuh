@@ -809,6 +809,13 @@ __device__ __forceinline__ float2 bcx2(float2 a) { return make_float2(a.x, a.x);
 __device__ __forceinline__ float2 bcy2(float2 a) { return make_float2(a.y, a.y); }
 // i a
 __device__ __forceinline__ float2 ipx(float2 a) { return make_float2(-a.y, a.x); }
+// a w and a conj(w) as w.x a +- w.y (i a): one packed multiply and one packed FMA
+__device__ __forceinline__ float2 pcmul(float2 a, float2 w) {
+  return __ffma2_rn(bcy2(w), ipx(a), __fmul2_rn(bcx2(w), a));
+}
+__device__ __forceinline__ float2 pcmulc(float2 a, float2 w) {
+  return __ffma2_rn(make_float2(-w.y, -w.y), ipx(a), __fmul2_rn(bcx2(w), a));
+}
 
 template <int R1, int R2, int MODE, int NP, int MINB>
 __global__ void __launch_bounds__(NP * R2, MINB)
@@ -1015,6 +1022,311 @@ f_p3s(float2* __restrict__ B, int n, int C, const float2* __restrict__ K, const 
       for (int n1 = 0; n1 < H; ++n1) colbase[c * cs + (long long)(R2 * n1 + t) * zs] = u[n1];
     }
     line_sync();  // the line's last readers are done before the next tile writes it
+  }
+}
+
+// z pass at 2n = 512 as two 256-point halves on a cluster of two CTAs
+// (FP32; 3x3 symmetric, divergence and Maxwell 6x6 mixing).  Only z < n = 256
+// of a z-line is nonzero, so with w = exp(-2 pi i / 512) its 512-point
+// spectrum splits by the parity r of the frequency,
+//   X[2k + r] = sum_{z < 256} (x[z] w^{z r}) W_256^{z k},
+// a full 256-point transform of x (r = 0) or of the twisted x[z] w^z (r = 1).
+// The kernel mixing is pointwise in k, so each half is mixed on its own, and
+// the inverse over all 512 frequencies is the sum of the halves' 256-point
+// inverses, the odd one twisted back by w^-z.  CTA r of a cluster owns half r
+// of the same pencils: it reads the pencils' inputs (the other CTA's reads of
+// the same lines are served by L2), stages the kernel octant entries of
+// z-parity r (half the z range of the other mirror-group kernels' slab), and
+// after its inverse transforms sends the half of its output that the other
+// CTA writes (z >= 128 from r = 0, z < 128 from r = 1) into that CTA's shared
+// memory (distributed shared memory; two cluster barriers per tile).  Every
+// thread carries three components of a vector (J or M for Maxwell: two thread
+// groups, the other vector's spectra parked in shared memory for the curl
+// terms) with 16 values each, as the 2n = 256 kernels do.  The twists are
+// folded into the radix-16 steps: with z = 16 n1 + t and k = k1 + 16 k2 the
+// odd half multiplies its inputs by W_32^{n1} (compile-time constants) before
+// the first step, the inter-step twiddles are w^{t (2 k1 + r)}, and the inverse
+// mirrors both.
+constexpr int oh_pick(int np, int hp) {
+  for (int o = 129; o < 145; ++o) {
+    const int v = (o * hp) % 8;
+    if (np >= 8 ? (v % 2 == 1) : (v == 2 || v == 6)) return o;
+  }
+  return 129;
+}
+
+template <int MODE, int NP>
+struct P3hCfg {
+  static constexpr int NG = (MODE == KM_MAXWELL6) ? 2 : 1;
+  static constexpr int NARR = (MODE == KM_SYM3) ? 6 : (MODE == KM_DIV ? 3 : 9);
+  static constexpr int NARRP = (NARR + 1) & ~1;  // values per slab point, padded to 16 bytes
+  static constexpr int R = 16, M = 512;
+  // Line pitch: 8-byte column accesses of the NP pencils x 32/NP threads of a
+  // warp fall on distinct bank pairs (at most two lanes per pair) when the
+  // pitch is 2 mod 16 for 8 pencils and 8 mod 16 for 4.
+  static constexpr int LS = ((R * (R + 1) + 15) / 16) * 16 + (NP >= 8 ? 2 : 8);
+  static constexpr int QW = NP + 1;
+  // Slab rows of OH >= 129 octant z entries (one parity, oz = 0..256): chosen so
+  // that the 16-byte reads of the 8 lanes of a quarter warp (8 pencils, or 4
+  // pencils x 2 frequencies) hit 8 distinct bank quads.
+  static constexpr int OH = oh_pick(NP, NARRP / 2);
+  static constexpr int NTHR = NG * NP * R;
+  static constexpr size_t SMEM = 8 * ((size_t)M + (size_t)NG * 3 * NP * LS + (size_t)QW * OH * NARRP);
+  // two CTAs per SM where 128 threads and the shared memory allow it
+  static constexpr int MINB = (NTHR <= 128 && 2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+// Every thread of both CTAs of the cluster: this thread's shared-memory writes
+// (local and remote) are released, the other threads' acquired.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// Address of p's counterpart in the shared memory of CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned peer_smem(const void* p, unsigned rank) {
+  unsigned d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n"
+               : "=r"(d)
+               : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+  return d;
+}
+__device__ __forceinline__ void st_peer(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+template <int MODE, int NP, int MINB, bool PK>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P3hCfg<MODE, NP>::NTHR, MINB)
+f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2* __restrict__ twg) {
+  typedef float T;
+  typedef float2 V;
+  typedef P3hCfg<MODE, NP> Cfg;
+  constexpr int NG = Cfg::NG, G = 3, GO = (MODE == KM_DIV) ? 1 : 3;
+  constexpr int NARR = Cfg::NARR, NARRP = Cfg::NARRP;
+  constexpr int R = Cfg::R, M = Cfg::M, NN = M / 2, NTX = M / NP, NTHR = Cfg::NTHR;
+  constexpr int NGROUPS = (M / 2 + 1) * (NTX / 2);
+  constexpr int LS = Cfg::LS, QW = Cfg::QW, OH = Cfg::OH, PF = R + 1, PI = R + 1;
+  constexpr int O = NN + 1;
+  constexpr long long O3 = (long long)O * O * O;
+  constexpr long long zs = (long long)M * M, cs = (long long)NN * zs;
+  static_assert(MODE == KM_SYM3 || MODE == KM_MAXWELL6, "half-spectrum z pass");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* tw = (V*)smraw;                // w^j, j < 512
+  V* sm = tw + M;                   // transpose lines [h][c][pencil], LS each
+  V* slab = sm + NG * G * NP * LS;  // [q < QW][oz / 2 < OH][a < NARRP], oz of parity r
+  const int r = (int)cluster_rank();
+  const int l = threadIdx.x % NP, t = (threadIdx.x / NP) % R, h = threadIdx.x / (NP * R);
+  const int b0 = blockIdx.y;
+  const int grp = blockIdx.x >> 1;  // both CTAs of a cluster take the same mirror group
+  if (grp >= NGROUPS) return;       // uniform over the cluster
+  const int kyp = grp / (NTX / 2), txp = grp - (grp / (NTX / 2)) * (NTX / 2);
+  const bool self_y = (kyp == 0 || kyp == M / 2);
+  {  // kernel slab <- K[a][2 ozh + r][kyp][NP txp + q], in flight while tile 0 starts
+    const V* src = K + (long long)kyp * O + NP * txp;
+    const int ohr = OH - r;  // 2 ozh + r <= n
+    for (int a = 0; a < NARR; ++a)
+      for (int idx = threadIdx.x; idx < ohr * QW; idx += NTHR) {
+        const int ozh = idx / QW, q = idx - ozh * QW;
+        cp_async<8>(slab + (q * OH + ozh) * NARRP + a, src + a * O3 + (long long)(2 * ozh + r) * O * O + q);
+      }
+    cp_async_commit();
+  }
+  for (int j = threadIdx.x; j < M; j += NTHR) tw[j] = twg[j];
+  V* s0 = sm + ((h * G) * NP + l) * LS;                    // this group's line of component c: s0 + c NP LS
+  const V* so = sm + (((NG - 1 - h) * G) * NP + l) * LS;  // the other vector's lines (Maxwell)
+  const unsigned s0_peer = peer_smem(s0, 1u - (unsigned)r);
+  V g[R];  // inputs of one component; the next one is loaded while the current one is transformed
+  auto load_comp = [&](const V* base, int c) {
+#pragma unroll
+    for (int n1 = 0; n1 < R; ++n1) g[n1] = base[c * cs + (long long)(R * n1 + t) * zs];
+  };
+  auto tile_base = [&](int v) {
+    const int ky = (v & 1) ? M - kyp : kyp;
+    const int tile = (v & 2) ? NTX - 1 - txp : txp;
+    return B + (long long)b0 * C * cs + (long long)(h * G) * cs + (long long)ky * M + tile * NP + l;
+  };
+  load_comp(tile_base(0), 0);
+#pragma unroll 1
+  for (int v = 0; v < 4; ++v) {
+    if ((v & 1) && self_y) continue;  // uniform over the cluster
+    const int ky = (v & 1) ? M - kyp : kyp;
+    const int kx = ((v & 2) ? NTX - 1 - txp : txp) * NP + l;
+    V* colbase = tile_base(v);
+    __syncthreads();  // twiddle table written; the previous tile's readers of the lines are done
+    // ---- forward: step 1 of every component into its line, step 2 from the lines
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+      V u[R];
+#pragma unroll
+      for (int n1 = 0; n1 < R; ++n1) u[n1] = g[n1];
+      if (c + 1 < G) load_comp(colbase, c + 1);
+      if (r) {
+#pragma unroll
+        for (int n1 = 1; n1 < R; ++n1) u[n1] = twc<32, -1, T>(u[n1], n1);
+      }
+      Dft<R, -1, T>::run(u);
+      V* s = s0 + c * NP * LS;
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) s[k1 * PF + t] = PK ? pcmul(u[k1], tw[t * (2 * k1 + r)])
+                                                          : cmul(u[k1], tw[t * (2 * k1 + r)]);
+    }
+    __syncthreads();
+    V X[G][R];  // X[c][k2] = spectrum of half r at k = t + 16 k2 (frequency 2k + r)
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+      const V* s = s0 + c * NP * LS + t * PF;
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) X[c][n2] = s[n2];
+      Dft<R, -1, T>::run(X[c]);
+    }
+    if (v == 0) cp_async_wait_all();  // the kernel slab (block-uniform)
+    __syncthreads();                  // lines free again; slab visible
+    // the next tile's first component, loaded during the mixing and the inverse
+    const int vn = self_y ? (v == 0 ? 2 : 4) : v + 1;
+    if (vn < 4) load_comp(tile_base(vn), 0);
+    if (NG == 2) {  // park the spectra for the other vector's curl terms
+#pragma unroll
+      for (int c = 0; c < G; ++c)
+#pragma unroll
+        for (int k2 = 0; k2 < R; ++k2) s0[c * NP * LS + t + R * k2] = X[c][k2];
+      __syncthreads();
+    }
+    // ---- kernel mixing on registers
+    {
+      const bool fy = ky > NN, fx = kx > NN;  // tile-uniform
+      const V* kq = slab + ((fx ? M - kx : kx) - NP * txp) * OH * NARRP;
+      float sg0[NARR], sg1[NARR];  // sign of array a for frequencies below and above n
+#pragma unroll
+      for (int a = 0; a < NARR; ++a) {
+        const int par = sym_parity(MODE == KM_DIV ? 6 + a : a);
+        const bool ng = ((par & 2) && fy) != ((par & 1) && fx);
+        sg0[a] = ng ? -1.f : 1.f;
+        sg1[a] = (ng != ((par & 4) != 0)) ? -1.f : 1.f;
+      }
+      const float sgc = (h == 0) ? 1.f : -1.f;  // + (P x M) in the J rows, - (P x J) in the M rows
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) {
+        // frequency 2 (t + 16 k2) + r is above n exactly when k2 >= 8 (compile time)
+        const bool fz = k2 >= R / 2;
+        const int ozh = fz ? NN - t - R * k2 - r : t + R * k2;
+        const float4* kp = (const float4*)(kq + ozh * NARRP);
+        V kv[NARRP];
+#pragma unroll
+        for (int a2 = 0; a2 < NARRP / 2; ++a2) {
+          const float4 q4 = kp[a2];
+          kv[2 * a2] = make_float2(q4.x, q4.y);
+          kv[2 * a2 + 1] = make_float2(q4.z, q4.w);
+        }
+#pragma unroll
+        for (int a = 0; a < NARR; ++a)
+          if (sym_parity(MODE == KM_DIV ? 6 + a : a) != 0) kv[a] = (fz ? sg1[a] : sg0[a]) * kv[a];
+        const V x0 = X[0][k2], x1 = X[1][k2], x2 = X[2][k2];
+        if (PK) {
+          // y += K x as y + K.x x + K.y (i x) on packed f32x2 instructions with
+          // broadcast operands; the J/M sign of the curl terms is in sgc
+          const V p0 = ipx(x0), p1 = ipx(x1), p2 = ipx(x2);
+          auto mac = [](V acc, V kk, V x, V ix) {
+            return __ffma2_rn(bcy2(kk), ix, __ffma2_rn(bcx2(kk), x, acc));
+          };
+          auto mul = [](V kk, V x, V ix) { return __ffma2_rn(bcy2(kk), ix, __fmul2_rn(bcx2(kk), x)); };
+          V y0 = mac(mac(mul(kv[0], x0, p0), kv[3], x1, p1), kv[4], x2, p2);
+          V y1 = mac(mac(mul(kv[3], x0, p0), kv[1], x1, p1), kv[5], x2, p2);
+          V y2 = mac(mac(mul(kv[4], x0, p0), kv[5], x1, p1), kv[2], x2, p2);
+          if (MODE == KM_MAXWELL6) {
+            const int k = t + R * k2;
+            const V o0 = so[k], o1 = so[NP * LS + k], o2 = so[2 * NP * LS + k];
+            const V q0 = ipx(o0), q1 = ipx(o1), q2 = ipx(o2);
+            const V c6 = sgc * kv[6], c7 = sgc * kv[7], c8 = sgc * kv[8];
+            const V n6 = -sgc * kv[6], n7 = -sgc * kv[7], n8 = -sgc * kv[8];
+            // J rows + (P x M), M rows - (P x J)
+            y0 = mac(mac(y0, c7, o2, q2), n8, o1, q1);
+            y1 = mac(mac(y1, c8, o0, q0), n6, o2, q2);
+            y2 = mac(mac(y2, c6, o1, q1), n7, o0, q0);
+          }
+          X[0][k2] = y0;
+          X[1][k2] = y1;
+          X[2][k2] = y2;
+        } else {
+          // symmetric 3x3: xx yy zz xy xz yz
+          V y0 = cmul(kv[0], x0) + cmul(kv[3], x1) + cmul(kv[4], x2);
+          V y1 = cmul(kv[3], x0) + cmul(kv[1], x1) + cmul(kv[5], x2);
+          V y2 = cmul(kv[4], x0) + cmul(kv[5], x1) + cmul(kv[2], x2);
+          if (MODE == KM_MAXWELL6) {
+            // J rows + (P x M), M rows - (P x J); P_a = kernel 6 + a
+            const int k = t + R * k2;
+            const V o0 = so[k], o1 = so[NP * LS + k], o2 = so[2 * NP * LS + k];
+            const V c0 = cmul(kv[7], o2) - cmul(kv[8], o1);
+            const V c1 = cmul(kv[8], o0) - cmul(kv[6], o2);
+            const V c2 = cmul(kv[6], o1) - cmul(kv[7], o0);
+            if (h == 0) {
+              y0 = y0 + c0;
+              y1 = y1 + c1;
+              y2 = y2 + c2;
+            } else {
+              y0 = y0 - c0;
+              y1 = y1 - c1;
+              y2 = y2 - c2;
+            }
+          }
+          X[0][k2] = y0;
+          X[1][k2] = y1;
+          X[2][k2] = y2;
+        }
+      }
+    }
+    if (NG == 2) __syncthreads();  // the other group has read the parked spectra
+    // ---- inverse: step A of every output component into its line
+#pragma unroll
+    for (int c = 0; c < GO; ++c) {
+      Dft<R, +1, T>::run(X[c]);
+      V* s = s0 + c * NP * LS;
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) s[n2 * PI + t] = PK ? pcmulc(X[c][n2], tw[n2 * (2 * t + r)])
+                                                          : cmulc(X[c][n2], tw[n2 * (2 * t + r)]);
+    }
+    __syncthreads();
+    // ---- step B; this CTA keeps outputs z = 16 n1 + t with n1 in [8 r, 8 r + 8)
+    V keep[GO][R / 2], send[GO][R / 2];
+#pragma unroll
+    for (int c = 0; c < GO; ++c) {
+      V u[R];
+      const V* s = s0 + c * NP * LS + t * PI;
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) u[k1] = s[k1];
+      Dft<R, +1, T>::run(u);
+      if (r) {
+#pragma unroll
+        for (int n1 = 1; n1 < R; ++n1) u[n1] = twc<32, +1, T>(u[n1], n1);
+#pragma unroll
+        for (int m = 0; m < R / 2; ++m) {
+          keep[c][m] = u[R / 2 + m];
+          send[c][m] = u[m];
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < R / 2; ++m) {
+          keep[c][m] = u[m];
+          send[c][m] = u[R / 2 + m];
+        }
+      }
+    }
+    cluster_barrier();  // both CTAs are done reading their lines
+#pragma unroll
+    for (int c = 0; c < GO; ++c)
+#pragma unroll
+      for (int m = 0; m < R / 2; ++m)
+        st_peer(s0_peer + 8u * (unsigned)(c * NP * LS + m * R + t), send[c][m]);
+    cluster_barrier();  // the other CTA's half has arrived
+#pragma unroll
+    for (int c = 0; c < GO; ++c)
+#pragma unroll
+      for (int m = 0; m < R / 2; ++m) {
+        const V y = keep[c][m] + s0[c * NP * LS + m * R + t];
+        colbase[c * cs + (long long)(R * (R / 2 * r + m) + t) * zs] = y;
+      }
   }
 }
 
@@ -1248,6 +1560,25 @@ struct FastPath {
       }
     }
   }
+  template <int MODE, int NP, bool PK>
+  static vie_status p3h(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
+    *done = false;
+    if constexpr (sizeof(T) != 4 || M != 512 || !(MODE == KM_SYM3 || MODE == KM_MAXWELL6)) {
+      return VIE_OK;  // FP32 at 2n = 512, the operator's kernel sets only
+    } else {
+      typedef P3hCfg<MODE, NP> Cfg;
+      if (2 * n != M) return VIE_OK;
+      const size_t sm = Cfg::SMEM;
+      if (sm > smem_optin()) return VIE_OK;
+      auto kern = f_p3h<MODE, NP, Cfg::MINB, PK>;
+      VIE_CK(allow_smem(kern, true));
+      const int groups = (M / 2 + 1) * (M / NP / 2);  // one cluster of two CTAs per mirror group
+      kern<<<dim3(2 * groups, nrhs), Cfg::NTHR, sm, st>>>((float2*)B, C, (const float2*)K, (const float2*)tw);
+      VIE_CK(cudaGetLastError());
+      *done = true;
+      return VIE_OK;
+    }
+  }
   template <int MODE, int NP>
   static vie_status p3b_ok(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
     constexpr int CMAX = ModeDim<MODE>::CI > ModeDim<MODE>::CO ? ModeDim<MODE>::CI : ModeDim<MODE>::CO;
@@ -1279,7 +1610,10 @@ struct FastPath {
       case 11: return p3t<MODE, 4, true>(B, n, C, K, nrhs, tw, done, st);
       case 12: return p3s<MODE, 8, 3>(B, n, C, K, nrhs, tw, done, st);
       case 13: return p3s<MODE, 8, 2>(B, n, C, K, nrhs, tw, done, st);
-      default: return p3s<MODE, 4, 5>(B, n, C, K, nrhs, tw, done, st);
+      case 14: return p3s<MODE, 4, 5>(B, n, C, K, nrhs, tw, done, st);
+      case 15: return p3h<MODE, 4, false>(B, n, C, K, nrhs, tw, done, st);
+      case 16: return p3h<MODE, 8, false>(B, n, C, K, nrhs, tw, done, st);
+      default: return p3h<MODE, 8, true>(B, n, C, K, nrhs, tw, done, st);
     }
   }
   // Run P3 variant `variant` (0..kP3Variants-1); *done = false if it does not apply to this shape.
@@ -1347,7 +1681,7 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
 // are scratch at this point); each keeps its best round and the fastest is
 // kept for the problem's (precision, mode).  VIE_TUNE=0 takes the first
 // applicable variant; VIE_P3_VARIANT=k forces variant k.
-static const int kP3Variants = 15;
+static const int kP3Variants = 18;
 static const int kP3Generic = 99;
 
 template <typename T, int R1, int R2>

@@ -448,7 +448,7 @@ def test_fast_and_generic_paths_agree_with_oracle(vie, n, monkeypatch):
         assert rel(y, yo) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", list(range(15)))
+@pytest.mark.parametrize("variant", list(range(18)))
 @pytest.mark.parametrize("kind,n,mu", [("helmholtz", 32, False), ("maxwell", 32, True), ("helmholtz", 64, False),
                                        ("helmholtz", 48, False), ("maxwell", 48, True), ("laplace", 96, False),
                                        ("helmholtz", 128, False)])
@@ -457,7 +457,7 @@ def test_every_zpass_variant_matches_oracle(vie, monkeypatch, variant, kind, n, 
     in every precision it applies to (the lane-pair variants 4-6 are FP32 only)."""
     import torch
 
-    assert vie.P3_VARIANTS == 15
+    assert vie.P3_VARIANTS == 18
     p = make_problem(kind, n, 2.0, mu, seed=8)
     op = operators.OracleProblem.from_problem(p)
     x = vi.random_field(n, op.ncomp, 10)[0]
@@ -522,6 +522,45 @@ def test_zpass_variants_at_2n_512(vie, monkeypatch):
             P.close()
             monkeypatch.delenv("VIE_P3_VARIANT", raising=False)
     assert any(v in ran for v in (0, 1, 2)), ran
+    assert 15 in ran and 16 in ran and 17 in ran, ran  # the half-spectrum cluster z pass exists at this shape
+
+
+@pytest.mark.parametrize("variant", [15, 16, 17])
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_half_spectrum_zpass_eigenfields_at_2n_512(vie, monkeypatch, variant, kind):
+    """The half-spectrum z pass (variants 15/16, 2n = 512 only: the even and odd
+    frequencies of each z-line on the two CTAs of a cluster) on the Lemma 2
+    eigenfields at 256^3, FP32: with eps = e I, Laplace maps grad psi to
+    (1 + h) grad psi and curl P to (1 - h) curl P, Helmholtz curl P to (1 + h) curl P."""
+    import torch
+
+    n = 256
+    e = 3.0
+    h = (e - 1) / (e + 1)
+    eps = np.zeros((9, n, n, n), np.complex128)
+    for a in range(3):
+        eps[4 * a] = e
+    omega = 0.0 if kind == "laplace" else 4 * math.pi
+    monkeypatch.setenv("VIE_P3_VARIANT", str(variant))
+    P = vie.Problem(kind, n, -1.0, 1.0, omega, to_dev(eps))
+    del eps
+    try:
+        grad, curl = gaussian_fields(n)
+        cases = [(curl, (1 - h) if kind == "laplace" else (1 + h))]
+        if kind == "laplace":
+            cases.append((grad, 1 + h))
+        for field, lam in cases:
+            xd = to_dev(field, torch.complex64)
+            yd = torch.empty_like(xd)
+            P.apply(xd, yd, vie.VIE_FP32)
+            torch.cuda.synchronize()
+            assert P.tune(vie.VIE_FP32) == variant
+            ref = lam * xd.to(torch.complex128)
+            err = float(torch.linalg.vector_norm(yd.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+            assert err <= 2e-5, (kind, variant, err)
+    finally:
+        P.close()
+        monkeypatch.delenv("VIE_P3_VARIANT", raising=False)
 
 
 def test_tune_entry_point(vie):
