@@ -74,8 +74,9 @@ def parse():
                          "Tables 2-5), laplace32 (electrostatic 32^3 solve to 1e-10, FP64 and mixed), selfconv "
                          "(E_2 / E_inf self-convergence on the paper's media, 30/42/70 against 210), maxwell326 "
                          "(the first experiment of Sec. 5.2 at 326^3: reduced Maxwell, oscillatory eps, w = 408, "
-                         "Bluestein transforms; set-up, FP32 apply and mixed solve to 1e-8); paper, selfconv and "
-                         "maxwell326 are not in the default run")
+                         "Bluestein transforms; set-up, FP32 apply and mixed solve to 1e-8), fig2 (Fig. 2: Bi-CGStab "
+                         "iterations to 1e-14 against w on the four media); paper, selfconv, maxwell326 and fig2 "
+                         "are not in the default run")
     ap.add_argument("--paper-n", type=int, default=70)
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--batched-rhs", type=int, default=64)
@@ -595,6 +596,53 @@ def leg_paper(args, dev):
     return out
 
 
+def leg_fig2(args, dev):
+    """Fig. 2 of Sec. 5.2: Bi-CGStab iterations to 1e-14 against w for the
+    Helmholtz and reduced Maxwell equations on the paper's four media ([0,1]^3,
+    E_in = (0, 0, exp(i w x)), FP64), w = 2 pi x {0.5, 1, 2, 3, 4, 5} (up to
+    w ~ 10 pi, the figure's range), on an n = --paper-n grid (the paper used
+    150; the counts are about mesh-independent, Tables 2-5).  A series stops at
+    the first solve that reaches the 3000-matvec cap, and no new solve starts
+    after 150 s, so the leg stays bounded."""
+    import torch
+
+    import paper_1805_04791_gb300 as vie
+    import vie_inputs as vi
+
+    n = args.paper_n
+    d = np.array([1.0, 0.0, 0.0])
+    pol = np.array([0.0, 0.0, 1.0])
+    sizes = (0.5, 1.0, 2.0, 3.0, 4.0, 5.0)
+    out = {"n": n, "tol": 1e-14, "matvec_cap": 3000, "series": []}
+    t_leg = time.perf_counter()
+    for medium in ("eps222", "eps234", "eps_dense", "eps444"):
+        eps = torch.from_numpy(vi.paper_medium(medium, n, 0.0, 1.0).reshape(9, -1).copy()).to(dev)
+        for kind in ("helmholtz", "maxwell"):
+            ser = {"medium": medium, "kind": kind, "points": []}
+            for size in sizes:
+                if time.perf_counter() - t_leg > 150.0:
+                    ser["stopped"] = "leg time budget"
+                    break
+                P = vie.Problem(kind, n, 0.0, 1.0, 2 * np.pi * size, eps)
+                b = torch.empty((3, n, n, n), dtype=torch.complex128, device=dev)
+                P.rhs(d, pol if kind == "maxwell" else None, 1, b)
+                J = torch.zeros_like(b)
+                t0 = time.perf_counter()
+                st, info = P.solve(b, J, tol=1e-14, max_inner=1500, mode=vie.VIE_SOLVE_BICGSTAB, allow_noconv=True)
+                torch.cuda.synchronize()
+                P.close()
+                ser["points"].append({"size": size, "omega": 2 * np.pi * size, "N_matvec": info.applies_fp64,
+                                      "rel_residual": info.rel_residual, "status": int(st),
+                                      "seconds": time.perf_counter() - t0})
+                if int(st) != 0:
+                    ser["stopped"] = "matvec cap"
+                    break
+            out["series"].append(ser)
+        del eps
+    out["leg_wall_s"] = time.perf_counter() - t_leg
+    return out
+
+
 def leg_selfconv(args, dev):
     """Self-convergence on the paper's media (Sec. 5.2; the E_2 / E_inf columns of
     Tables 2-5): reduced Maxwell, E_in = (0, 0, exp(i w x)) on [0,1]^3, FP64 GMRES to
@@ -899,7 +947,7 @@ def run_ours(args):
     for leg in [x for x in args.legs.split(",") if x]:
         t0 = time.perf_counter()
         fn = {"batched": leg_batched, "maxwell256": leg_maxwell256, "maxwell326": leg_maxwell326, "serve": leg_serve,
-              "paper": leg_paper,
+              "paper": leg_paper, "fig2": leg_fig2,
               "laplace32": leg_laplace32, "selfconv": leg_selfconv}[leg]
         try:
             extra[leg] = fn(args, dev)

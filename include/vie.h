@@ -259,11 +259,13 @@ vie_status vie_problem_destroy(vie_problem* P);
  * 12/13/14 (FP32, 3x3 symmetric and divergence kernel sets, same sizes) slim
  * component-group CTAs of 8/8/4 pencils sized for 3/2/5 CTAs per SM: one
  * transpose line per pencil shared by the components in turn, 16-byte
- * shared-memory reads, packed f32x2 kernel mixing; 15/16/17 (FP32, 2n = 512,
- * 3x3 symmetric and Maxwell kernel sets) the even and odd frequencies of each
- * z-line as two 256-point transforms on the two CTAs of a thread-block
+ * shared-memory reads, packed f32x2 kernel mixing; 15/16/17/18 (FP32, 2n =
+ * 512, 3x3 symmetric and Maxwell kernel sets) the even and odd frequencies of
+ * each z-line as two 256-point transforms on the two CTAs of a thread-block
  * cluster, the inverse halves summed through distributed shared memory, with
- * 4/8/8 pencils per CTA (17: packed f32x2 twiddles and kernel mixing).
+ * 4/8/8/8 pencils per CTA (17: packed f32x2 twiddles and kernel mixing; 18: a
+ * grid of co-resident clusters, each walking several mirror groups and loading
+ * the next one's kernel entries and first inputs during the current one).
  * Every candidate runs once untimed, then two rounds of three timed launches;
  * each keeps its best round and the fastest is chosen.  VIE_DF64 has one fixed
  * schedule (*variant = -1).  vie_apply

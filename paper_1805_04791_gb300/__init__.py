@@ -24,7 +24,7 @@ VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA, VIE_ENOCONV, VIE_ENAN, VIE_ETIMEOUT, 
 VIE_LAPLACE, VIE_HELMHOLTZ, VIE_MAXWELL = range(3)
 VIE_FP64, VIE_FP32, VIE_DF64 = 0, 1, 2  # VIE_DF64: FP64 vectors, double-word arithmetic
 VIE_SOLVE_FP64, VIE_SOLVE_MIXED, VIE_SOLVE_BICGSTAB = 0, 1, 2
-P3_VARIANTS = 18  # z-pass schedules vie_tune chooses from (include/vie.h)
+P3_VARIANTS = 19  # z-pass schedules vie_tune chooses from (include/vie.h)
 KINDS = {"laplace": VIE_LAPLACE, "helmholtz": VIE_HELMHOLTZ, "maxwell": VIE_MAXWELL}
 STATUS_NAMES = {0: "VIE_OK", 1: "VIE_EINVAL", 2: "VIE_ENOMEM", 3: "VIE_ECUDA", 4: "VIE_ENOCONV",
                 5: "VIE_ENAN", 6: "VIE_ETIMEOUT", 7: "VIE_EBUSY"}

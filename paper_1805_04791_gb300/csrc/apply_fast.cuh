@@ -1098,7 +1098,7 @@ __device__ __forceinline__ void st_peer(unsigned addr, float2 v) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
-template <int MODE, int NP, int MINB, bool PK>
+template <int MODE, int NP, int MINB, bool PK, bool PS>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P3hCfg<MODE, NP>::NTHR, MINB)
 f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2* __restrict__ twg) {
   typedef float T;
@@ -1120,12 +1120,16 @@ f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2*
   const int r = (int)cluster_rank();
   const int l = threadIdx.x % NP, t = (threadIdx.x / NP) % R, h = threadIdx.x / (NP * R);
   const int b0 = blockIdx.y;
-  const int grp = blockIdx.x >> 1;  // both CTAs of a cluster take the same mirror group
-  if (grp >= NGROUPS) return;       // uniform over the cluster
-  const int kyp = grp / (NTX / 2), txp = grp - (grp / (NTX / 2)) * (NTX / 2);
-  const bool self_y = (kyp == 0 || kyp == M / 2);
-  {  // kernel slab <- K[a][2 ozh + r][kyp][NP txp + q], in flight while tile 0 starts
-    const V* src = K + (long long)kyp * O + NP * txp;
+  // Both CTAs of a cluster take the same mirror groups: one (PS false), or
+  // grp, grp + gstride, ... on a grid of co-resident clusters (PS true).
+  const int gstride = PS ? (int)(gridDim.x >> 1) : NGROUPS;
+  int grp = blockIdx.x >> 1;
+  if (grp >= NGROUPS) return;  // uniform over the cluster
+  auto g_kyp = [&](int gr) { return gr / (NTX / 2); };
+  auto g_txp = [&](int gr) { return gr - (gr / (NTX / 2)) * (NTX / 2); };
+  // kernel slab <- K[a][2 ozh + r][kyp][NP txp + q], in flight while other work runs
+  auto slab_issue = [&](int gr) {
+    const V* src = K + (long long)g_kyp(gr) * O + NP * g_txp(gr);
     const int ohr = OH - r;  // 2 ozh + r <= n
     for (int a = 0; a < NARR; ++a)
       for (int idx = threadIdx.x; idx < ohr * QW; idx += NTHR) {
@@ -1133,7 +1137,8 @@ f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2*
         cp_async<8>(slab + (q * OH + ozh) * NARRP + a, src + a * O3 + (long long)(2 * ozh + r) * O * O + q);
       }
     cp_async_commit();
-  }
+  };
+  slab_issue(grp);
   for (int j = threadIdx.x; j < M; j += NTHR) tw[j] = twg[j];
   V* s0 = sm + ((h * G) * NP + l) * LS;                    // this group's line of component c: s0 + c NP LS
   const V* so = sm + (((NG - 1 - h) * G) * NP + l) * LS;  // the other vector's lines (Maxwell)
@@ -1143,18 +1148,23 @@ f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2*
 #pragma unroll
     for (int n1 = 0; n1 < R; ++n1) g[n1] = base[c * cs + (long long)(R * n1 + t) * zs];
   };
-  auto tile_base = [&](int v) {
-    const int ky = (v & 1) ? M - kyp : kyp;
-    const int tile = (v & 2) ? NTX - 1 - txp : txp;
+  auto tile_base = [&](int gr, int v) {
+    const int ky = (v & 1) ? M - g_kyp(gr) : g_kyp(gr);
+    const int tile = (v & 2) ? NTX - 1 - g_txp(gr) : g_txp(gr);
     return B + (long long)b0 * C * cs + (long long)(h * G) * cs + (long long)ky * M + tile * NP + l;
   };
-  load_comp(tile_base(0), 0);
+  load_comp(tile_base(grp, 0), 0);
+#pragma unroll 1
+  for (; grp < NGROUPS; grp += gstride) {
+  const int kyp = g_kyp(grp), txp = g_txp(grp);
+  const bool self_y = (kyp == 0 || kyp == M / 2);
+  const int ngrp = grp + gstride;  // the cluster's next group (PS)
 #pragma unroll 1
   for (int v = 0; v < 4; ++v) {
     if ((v & 1) && self_y) continue;  // uniform over the cluster
     const int ky = (v & 1) ? M - kyp : kyp;
     const int kx = ((v & 2) ? NTX - 1 - txp : txp) * NP + l;
-    V* colbase = tile_base(v);
+    V* colbase = tile_base(grp, v);
     __syncthreads();  // twiddle table written; the previous tile's readers of the lines are done
     // ---- forward: step 1 of every component into its line, step 2 from the lines
 #pragma unroll
@@ -1186,7 +1196,8 @@ f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2*
     __syncthreads();                  // lines free again; slab visible
     // the next tile's first component, loaded during the mixing and the inverse
     const int vn = self_y ? (v == 0 ? 2 : 4) : v + 1;
-    if (vn < 4) load_comp(tile_base(vn), 0);
+    if (vn < 4) load_comp(tile_base(grp, vn), 0);
+    else if (PS && ngrp < NGROUPS) load_comp(tile_base(ngrp, 0), 0);
     if (NG == 2) {  // park the spectra for the other vector's curl terms
 #pragma unroll
       for (int c = 0; c < G; ++c)
@@ -1288,6 +1299,8 @@ f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2*
                                                           : cmulc(X[c][n2], tw[n2 * (2 * t + r)]);
     }
     __syncthreads();
+    // every thread is past the group's last mixing: the slab may take the next group's kernel
+    if (PS && vn >= 4 && ngrp < NGROUPS) slab_issue(ngrp);
     // ---- step B; this CTA keeps outputs z = 16 n1 + t with n1 in [8 r, 8 r + 8)
     V keep[GO][R / 2], send[GO][R / 2];
 #pragma unroll
@@ -1327,6 +1340,7 @@ f_p3h(float2* __restrict__ B, int C, const float2* __restrict__ K, const float2*
         const V y = keep[c][m] + s0[c * NP * LS + m * R + t];
         colbase[c * cs + (long long)(R * (R / 2 * r + m) + t) * zs] = y;
       }
+  }
   }
 }
 
@@ -1560,7 +1574,7 @@ struct FastPath {
       }
     }
   }
-  template <int MODE, int NP, bool PK>
+  template <int MODE, int NP, bool PK, bool PS = false>
   static vie_status p3h(V* B, int n, int C, const V* K, int nrhs, const V* tw, bool* done, cudaStream_t st) {
     *done = false;
     if constexpr (sizeof(T) != 4 || M != 512 || !(MODE == KM_SYM3 || MODE == KM_MAXWELL6)) {
@@ -1570,9 +1584,22 @@ struct FastPath {
       if (2 * n != M) return VIE_OK;
       const size_t sm = Cfg::SMEM;
       if (sm > smem_optin()) return VIE_OK;
-      auto kern = f_p3h<MODE, NP, Cfg::MINB, PK>;
+      auto kern = f_p3h<MODE, NP, Cfg::MINB, PK, PS>;
       VIE_CK(allow_smem(kern, true));
-      const int groups = (M / 2 + 1) * (M / NP / 2);  // one cluster of two CTAs per mirror group
+      int groups = (M / 2 + 1) * (M / NP / 2);  // one cluster of two CTAs per mirror group
+      if (PS) {  // as many clusters as are co-resident; each walks several mirror groups
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * groups, nrhs);
+        cfg.blockDim = dim3(Cfg::NTHR);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = st;
+        int nclu = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclu, (const void*)kern, &cfg) != cudaSuccess || nclu < 1) {
+          (void)cudaGetLastError();
+          return VIE_OK;  // not applicable on this device
+        }
+        groups = std::max(1, std::min(groups, nclu / nrhs));
+      }
       kern<<<dim3(2 * groups, nrhs), Cfg::NTHR, sm, st>>>((float2*)B, C, (const float2*)K, (const float2*)tw);
       VIE_CK(cudaGetLastError());
       *done = true;
@@ -1613,7 +1640,8 @@ struct FastPath {
       case 14: return p3s<MODE, 4, 5>(B, n, C, K, nrhs, tw, done, st);
       case 15: return p3h<MODE, 4, false>(B, n, C, K, nrhs, tw, done, st);
       case 16: return p3h<MODE, 8, false>(B, n, C, K, nrhs, tw, done, st);
-      default: return p3h<MODE, 8, true>(B, n, C, K, nrhs, tw, done, st);
+      case 17: return p3h<MODE, 8, true>(B, n, C, K, nrhs, tw, done, st);
+      default: return p3h<MODE, 8, false, true>(B, n, C, K, nrhs, tw, done, st);
     }
   }
   // Run P3 variant `variant` (0..kP3Variants-1); *done = false if it does not apply to this shape.
@@ -1681,7 +1709,7 @@ vie_status fast_pass(int pass, vie_problem* P, const KernelSet& K, const void* i
 // are scratch at this point); each keeps its best round and the fastest is
 // kept for the problem's (precision, mode).  VIE_TUNE=0 takes the first
 // applicable variant; VIE_P3_VARIANT=k forces variant k.
-static const int kP3Variants = 18;
+static const int kP3Variants = 19;
 static const int kP3Generic = 99;
 
 template <typename T, int R1, int R2>

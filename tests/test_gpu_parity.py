@@ -448,7 +448,7 @@ def test_fast_and_generic_paths_agree_with_oracle(vie, n, monkeypatch):
         assert rel(y, yo) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", list(range(18)))
+@pytest.mark.parametrize("variant", list(range(19)))
 @pytest.mark.parametrize("kind,n,mu", [("helmholtz", 32, False), ("maxwell", 32, True), ("helmholtz", 64, False),
                                        ("helmholtz", 48, False), ("maxwell", 48, True), ("laplace", 96, False),
                                        ("helmholtz", 128, False)])
@@ -457,7 +457,7 @@ def test_every_zpass_variant_matches_oracle(vie, monkeypatch, variant, kind, n, 
     in every precision it applies to (the lane-pair variants 4-6 are FP32 only)."""
     import torch
 
-    assert vie.P3_VARIANTS == 18
+    assert vie.P3_VARIANTS == 19
     p = make_problem(kind, n, 2.0, mu, seed=8)
     op = operators.OracleProblem.from_problem(p)
     x = vi.random_field(n, op.ncomp, 10)[0]
@@ -522,13 +522,13 @@ def test_zpass_variants_at_2n_512(vie, monkeypatch):
             P.close()
             monkeypatch.delenv("VIE_P3_VARIANT", raising=False)
     assert any(v in ran for v in (0, 1, 2)), ran
-    assert 15 in ran and 16 in ran and 17 in ran, ran  # the half-spectrum cluster z pass exists at this shape
+    assert all(v in ran for v in (15, 16, 17, 18)), ran  # the half-spectrum cluster z pass exists at this shape
 
 
-@pytest.mark.parametrize("variant", [15, 16, 17])
+@pytest.mark.parametrize("variant", [15, 16, 17, 18])
 @pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
 def test_half_spectrum_zpass_eigenfields_at_2n_512(vie, monkeypatch, variant, kind):
-    """The half-spectrum z pass (variants 15/16, 2n = 512 only: the even and odd
+    """The half-spectrum z pass (variants 15-18, 2n = 512 only: the even and odd
     frequencies of each z-line on the two CTAs of a cluster) on the Lemma 2
     eigenfields at 256^3, FP32: with eps = e I, Laplace maps grad psi to
     (1 + h) grad psi and curl P to (1 - h) curl P, Helmholtz curl P to (1 + h) curl P."""
