@@ -59,6 +59,9 @@
  *                       with an FP32 apply of a small correction.
  * - VIE_GRAPHS=0        single right-hand-side GMRES steps are launched kernel by
  *                       kernel instead of being replayed from captured CUDA graphs.
+ * - VIE_ARNOLDI_SHIFT=0 GMRES orthogonalises A v instead of (A - I) v (the
+ *                       same Krylov space; with the shift, 1 is added to each
+ *                       diagonal Hessenberg entry).
  */
 #ifndef VIE_H
 #define VIE_H
